@@ -1,0 +1,212 @@
+/*
+ * eh.h -- C ABI of the GB300 pattern-count engine (libeh.so).
+ *
+ * The engine evaluates COUNT(*) graph pattern queries by the generic
+ * worst-case optimal join (EmptyHeaded, Aberger et al., SIGMOD'16,
+ * arXiv 1503.02368, Algorithm 1) over a two-level trie of sorted 32-bit
+ * neighbour sets (Sec. 2.2), each set stored in a density-chosen uint or
+ * bitset layout (Sec. 4.1, set-level rule of Sec. 4.4).  Its operations are
+ * those of the paper's execution engine (Table 2): R[t] (the set under a
+ * prefix), for-x-in-xs, and xs ∩ ys, composed for the triangle, 4-clique and
+ * lollipop queries of Table 1.
+ *
+ * Conventions for every call:
+ *   - Every function returns an eh_status and never aborts, exits or traps.
+ *     On failure eh_last_error() gives a message (thread-local, valid until
+ *     the next call on the same thread).
+ *   - Host pointers are owned by the caller; the library copies what it
+ *     needs before returning.  Device pointers are accepted only where a flag
+ *     says so.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that return host results synchronise that stream before returning.
+ *   - Vertex ids are uint32 in [0, n_vertices).  Direction is ignored;
+ *     self-loops and repeated pairs are dropped (the graph is simple and
+ *     undirected).
+ *   - Counts are exact uint64.  A count that would exceed 2^64-1 returns
+ *     EH_EOVERFLOW.
+ */
+#ifndef EH_H
+#define EH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EH_OK = 0,
+    EH_EINVAL = 1,    /* bad argument: id >= n_vertices, NULL pointer, unknown pattern */
+    EH_ENOMEM = 2,    /* device or host allocation failed; nothing leaked */
+    EH_ECUDA = 3,     /* a CUDA runtime error (message in eh_last_error) */
+    EH_ETIMEOUT = 4,  /* a bounded device-side wait ran out; the context stays usable */
+    EH_EOVERFLOW = 5, /* a count exceeds uint64 */
+    EH_EBUSY = 6      /* admission refused: the query does not fit the memory budget now */
+} eh_status;
+
+/* Table 1 patterns, COUNT(*) semantics:
+ *   EH_TRIANGLE  Triangle(x,y,z) :- R(x,y),S(y,z),T(x,z)          each triangle once
+ *   EH_CLIQUE4   4Clique(x,y,z,w) :- R,S,T,U,V,Q (all six pairs)   each 4-clique once
+ *   EH_LOLLIPOP  Lollipop(x,y,z,w) :- R(x,y),S(y,z),T(x,z),U(x,w)  on the undirected
+ *                relation, datalog join semantics (ordered tuples, w unconstrained):
+ *                sum_x 2 t(x) d(x), with t(x) the triangles at x and d(x) its degree
+ *   EH_LOLLIPOP_DISTINCT  lollipop subgraphs (triangle + pendant edge, w outside the
+ *                triangle), each once: sum_x t(x) (d(x) - 2)                          */
+typedef enum {
+    EH_TRIANGLE = 0,
+    EH_CLIQUE4 = 1,
+    EH_LOLLIPOP = 2,
+    EH_LOLLIPOP_DISTINCT = 3
+} eh_pattern;
+
+typedef struct eh_trie eh_trie; /* opaque, device-resident, owned by the library */
+
+/* eh_build_trie options.  Pass NULL for the defaults (tau 32, input on host). */
+typedef struct {
+    /* Set-level layout rule (Sec. 4.4): a set S is stored as a bitset when its
+     * range max-min+1 is at most bitset_tau bits per element (range <= tau*|S|).
+     * 0 = every set uint (the paper's relation-level "-R" configuration);
+     * 0xFFFFFFFF = every non-empty set bitset.  The paper's value is 256 (one
+     * AVX register per element). */
+    uint32_t bitset_tau;
+    uint32_t min_bitset_len; /* sets shorter than this stay uint (default 0) */
+    uint32_t flags;          /* EH_BUILD_* */
+} eh_build_opts;
+
+#define EH_BUILD_DEVICE_INPUT 1u /* src/dst are device pointers (read on `stream`) */
+
+/* Execution knobs for the intersection kernels.  NULL = defaults. */
+typedef struct {
+    uint32_t gallop_ratio;  /* uint∩uint: gallop when |large| > ratio*|small| (Sec. 4.2's 32:1); default 32 */
+    uint32_t light_max;     /* vertices with |N+(u)| <= light_max run one warp each; default 32 */
+    uint32_t cta_warps;     /* warps per CTA for heavy vertices (4, 8 or 16); default 8 */
+    uint32_t flags;         /* reserved, 0 */
+} eh_exec_opts;
+
+typedef struct {
+    uint32_t n_vertices;   /* id space */
+    uint32_t n_active;     /* vertices with degree > 0 */
+    uint64_t n_edges;      /* unique undirected edges m */
+    uint32_t max_degree;   /* max d(v) */
+    uint32_t max_out_degree; /* max |N+(v)| of the pruned (degree-oriented) relation */
+    uint64_t n_bitset_sets;  /* pruned sets stored as bitsets */
+    uint64_t n_nonempty_sets;
+    uint64_t bitset_words;   /* 32-bit words in the bitset pool */
+    double density_skew;     /* Pearson's first skewness 3(mean-mode)/sigma of the degrees (Sec. 4 footnote) */
+    uint64_t device_bytes;   /* device memory held by the trie */
+    uint32_t bitset_tau;
+    uint32_t reserved;
+} eh_trie_stats;
+
+/* One query of a batch: pattern over the subgraph induced by
+ * subset_pool[subset_off .. subset_off+subset_len) (original ids; order and
+ * repeats are irrelevant).  subset_len == 0 means the whole graph. */
+typedef struct {
+    uint32_t pattern;   /* eh_pattern */
+    uint32_t subset_len;
+    uint64_t subset_off;
+} eh_query;
+
+/* eh_build_trie -- edge list to a device-resident trie (Sec. 2.2; pruning
+ * and degree ordering of Sec. 5.2.1 / App. A.1.1; layout rule of Sec. 4.4).
+ *   src, dst    n_edges vertex ids each (host, or device with EH_BUILD_DEVICE_INPUT)
+ *   n_vertices  id space; every id must be < n_vertices, else EH_EINVAL
+ *   out         receives the trie; release it with eh_free_trie.
+ * Builds: the simple undirected edge set; new ids by (degree desc, original
+ * id asc); the symmetric trie N(v) and the pruned trie N+(v) = {u in N(v) :
+ * u < v} (new ids), each set sorted, 16-byte aligned; a bitset copy of each
+ * pruned set the layout rule selects; the per-vertex work list. */
+eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uint64_t n_edges, uint32_t n_vertices,
+                        const eh_build_opts *opts, void *stream, eh_trie **out);
+
+/* eh_count -- COUNT(*) of `pattern` over the whole graph (subset == NULL or
+ * subset_len == 0) or over the subgraph induced by `subset` (host array of
+ * original ids, any order, repeats allowed).  Writes *out_count (host). */
+eh_status eh_count(const eh_trie *trie, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
+                   void *stream, uint64_t *out_count);
+
+/* eh_count_ex -- as eh_count with explicit execution knobs (NULL = defaults). */
+eh_status eh_count_ex(const eh_trie *trie, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
+                      const eh_exec_opts *xopts, void *stream, uint64_t *out_count);
+
+/* eh_count_async -- whole-graph count enqueued on `stream` with no host
+ * synchronisation: the uint64 result is written to device memory
+ * d_out_count (8 bytes, caller-owned, 8-byte aligned).  Errors found on the
+ * device (a timed-out wait, an overflow) are reported by the next
+ * eh_count_status call. */
+eh_status eh_count_async(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
+                         uint64_t *d_out_count);
+
+/* eh_count_status -- synchronises `stream` and returns the device-side
+ * status word of the trie's last asynchronous counts (then clears it). */
+eh_status eh_count_status(const eh_trie *trie, void *stream);
+
+/* eh_vertex_triangles -- t(x), the number of triangles containing x, for
+ * every original id x (host array of n_vertices uint64). */
+eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint64_t *out_t);
+
+/* eh_count_batch -- n_queries independent queries in one persistent launch.
+ * Each query's count goes to out_counts[i] and its status to out_status[i]
+ * (a failing query does not fail the others; the call returns the first
+ * non-OK status, or EH_OK).  subset_pool is a host array of pool_len ids. */
+eh_status eh_count_batch(const eh_trie *trie, const eh_query *queries, uint32_t n_queries,
+                         const uint32_t *subset_pool, uint64_t pool_len, void *stream, uint64_t *out_counts,
+                         eh_status *out_status);
+
+/* eh_count_batch_ex -- as eh_count_batch with explicit knobs; `mode` 0 runs
+ * the batch as one persistent launch, 1 runs it one query at a time (the
+ * one-launch-per-query baseline, same kernels, same results). */
+eh_status eh_count_batch_ex(const eh_trie *trie, const eh_query *queries, uint32_t n_queries,
+                            const uint32_t *subset_pool, uint64_t pool_len, const eh_exec_opts *xopts,
+                            uint32_t mode, void *stream, uint64_t *out_counts, eh_status *out_status);
+
+eh_status eh_trie_stats_get(const eh_trie *trie, eh_trie_stats *out);
+
+/* eh_trie_export -- copies the trie to host arrays for inspection (tests).
+ * Any output pointer may be NULL.  Sizes: new_to_old[n], out_off[n+1]
+ * (element offsets into out_nbr, 16-byte aligned sets), out_len[n],
+ * out_nbr[out_off[n]], bits_lo[n] (first value covered by the bitset, or
+ * 0xFFFFFFFF for uint sets), bits_nwords[n], bits_off[n] (word offsets into
+ * out_words), out_words[total bitset words].  `which` 0 = pruned trie N+,
+ * 1 = symmetric trie N (no bitsets). */
+eh_status eh_trie_export(const eh_trie *trie, uint32_t which, uint32_t *new_to_old, uint64_t *out_off,
+                         uint32_t *out_len, uint32_t *out_nbr, uint32_t *bits_lo, uint32_t *bits_nwords,
+                         uint64_t *bits_off, uint32_t *out_words);
+
+void eh_free_trie(eh_trie *trie);
+
+const char *eh_last_error(void);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop over a resident trie: submit() admits a query when its
+ * estimated device footprint fits the memory budget (else EH_EBUSY), queued
+ * queries are batched onto the device as they arrive and slots free up
+ * (continuous batching, several batches in flight on separate streams), and
+ * poll()/wait() return each query's result. */
+typedef struct eh_server eh_server;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    uint64_t batches;        /* device batches launched */
+    uint64_t bytes_in_use;   /* admitted footprint not yet released */
+    uint64_t peak_bytes;
+    double mean_batch;       /* queries per batch */
+} eh_server_stats;
+
+eh_status eh_server_create(const eh_trie *trie, uint64_t memory_budget_bytes, uint32_t max_batch,
+                           uint32_t max_inflight, eh_server **out);
+/* Copies subset[0..subset_len) and queues the query; *ticket identifies it. */
+eh_status eh_server_submit(eh_server *s, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
+                           uint64_t *ticket);
+/* 1 if done (result in *count, *status), 0 if pending; EH_EINVAL for an unknown ticket. */
+eh_status eh_server_poll(eh_server *s, uint64_t ticket, int *done, uint64_t *count, eh_status *status);
+/* Blocks up to timeout_ms (0 = no limit) for the ticket. */
+eh_status eh_server_wait(eh_server *s, uint64_t ticket, uint32_t timeout_ms, uint64_t *count,
+                         eh_status *status);
+eh_status eh_server_stats_get(eh_server *s, eh_server_stats *out);
+void eh_server_destroy(eh_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EH_H */

@@ -1,0 +1,172 @@
+"""CPU oracle for the pattern COUNT(*) queries (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package.  The product path never does.  The C source
+(``eh_oracle.c``) is a plain nested-loop generic join with scalar merges.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "eh_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        ip = ctypes.POINTER(ctypes.c_int)
+        vp = ctypes.c_void_p
+        L.oracle_canon.restype = ctypes.c_int64
+        L.oracle_canon.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_uint32, u32p, u32p]
+        L.oracle_graph_new.restype = vp
+        L.oracle_graph_new.argtypes = [ctypes.c_uint32, u32p, u32p, ctypes.c_uint64]
+        L.oracle_graph_free.argtypes = [vp]
+        L.oracle_graph_n.restype = ctypes.c_uint32
+        L.oracle_graph_n.argtypes = [vp]
+        L.oracle_graph_m.restype = ctypes.c_uint64
+        L.oracle_graph_m.argtypes = [vp]
+        L.oracle_neighbours.restype = ctypes.c_uint64
+        L.oracle_neighbours.argtypes = [vp, ctypes.c_uint32, u32p]
+        for f in (L.oracle_triangles, L.oracle_clique4):
+            f.restype = ctypes.c_uint64
+            f.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip]
+        for f in (L.oracle_lollipop, L.oracle_lollipop_distinct):
+            f.restype = ctypes.c_uint64
+            f.argtypes = [vp, ctypes.c_int, ip]
+        L.oracle_vertex_triangles.argtypes = [vp, u32p, ctypes.c_uint64, u64p]
+        L.oracle_induced.restype = vp
+        L.oracle_induced.argtypes = [vp, u32p, ctypes.c_uint64]
+        L.oracle_layout_is_bitset.restype = ctypes.c_int
+        L.oracle_layout_is_bitset.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32]
+        L.oracle_degree_order.argtypes = [vp, u32p]
+        _lib = L
+    return _lib
+
+
+def _u32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def _threads(t):
+    return int(t) if t else 1
+
+
+class OverflowError64(ArithmeticError):
+    pass
+
+
+def canon(src, dst, n):
+    """Canonical simple undirected edge set (a<b), sorted, unique."""
+    src = np.ascontiguousarray(src, np.uint32)
+    dst = np.ascontiguousarray(dst, np.uint32)
+    a = np.empty(len(src), np.uint32)
+    b = np.empty(len(src), np.uint32)
+    m = lib().oracle_canon(_u32p(src), _u32p(dst), len(src), n, _u32p(a), _u32p(b))
+    if m == -1:
+        raise ValueError("vertex id >= n")
+    if m < 0:
+        raise MemoryError("oracle_canon")
+    return a[:m].copy(), b[:m].copy()
+
+
+class Graph:
+    """Simple undirected graph as a two-level trie (oracle side)."""
+
+    def __init__(self, n, src=None, dst=None, _handle=None):
+        if _handle is not None:
+            self._h = _handle
+            return
+        a, b = canon(src, dst, n)
+        self._h = lib().oracle_graph_new(n, _u32p(a), _u32p(b), len(a))
+        if not self._h:
+            raise MemoryError("oracle graph")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.oracle_graph_free(h)
+            self._h = None
+
+    @property
+    def n(self):
+        return int(lib().oracle_graph_n(self._h))
+
+    @property
+    def m(self):
+        return int(lib().oracle_graph_m(self._h))
+
+    def neighbours(self, v):
+        d = lib().oracle_neighbours(self._h, v, None)
+        out = np.empty(d, np.uint32)
+        lib().oracle_neighbours(self._h, v, _u32p(out))
+        return out
+
+    def degrees(self):
+        return np.array([lib().oracle_neighbours(self._h, v, None) for v in range(self.n)], np.uint64)
+
+    def _chk(self, val, ovf):
+        if ovf.value:
+            raise OverflowError64("count exceeds uint64")
+        return int(val)
+
+    def triangles(self, pruned=True, nthreads=1):
+        o = ctypes.c_int(0)
+        return self._chk(lib().oracle_triangles(self._h, int(pruned), _threads(nthreads), ctypes.byref(o)), o)
+
+    def clique4(self, pruned=True, nthreads=1):
+        o = ctypes.c_int(0)
+        return self._chk(lib().oracle_clique4(self._h, int(pruned), _threads(nthreads), ctypes.byref(o)), o)
+
+    def lollipop(self, nthreads=1):
+        o = ctypes.c_int(0)
+        return self._chk(lib().oracle_lollipop(self._h, _threads(nthreads), ctypes.byref(o)), o)
+
+    def lollipop_distinct(self, nthreads=1):
+        o = ctypes.c_int(0)
+        return self._chk(lib().oracle_lollipop_distinct(self._h, _threads(nthreads), ctypes.byref(o)), o)
+
+    def count(self, pattern, nthreads=1):
+        """pattern: 'triangle' | 'clique4' | 'lollipop' | 'lollipop_distinct'."""
+        return {"triangle": self.triangles, "clique4": self.clique4, "lollipop": self.lollipop,
+                "lollipop_distinct": self.lollipop_distinct}[pattern](nthreads=nthreads)
+
+    def vertex_triangles(self, verts):
+        verts = np.ascontiguousarray(verts, np.uint32)
+        out = np.empty(len(verts), np.uint64)
+        lib().oracle_vertex_triangles(self._h, _u32p(verts), len(verts),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        return out
+
+    def induced(self, subset):
+        subset = np.ascontiguousarray(subset, np.uint32)
+        h = lib().oracle_induced(self._h, _u32p(subset), len(subset))
+        if not h:
+            raise ValueError("subset id >= n")
+        return Graph(0, _handle=h)
+
+    def degree_order(self):
+        out = np.empty(self.n, np.uint32)
+        lib().oracle_degree_order(self._h, _u32p(out))
+        return out
+
+
+def layout_is_bitset(sorted_set, tau):
+    s = np.ascontiguousarray(sorted_set, np.uint32)
+    return bool(lib().oracle_layout_is_bitset(_u32p(s), len(s), tau))

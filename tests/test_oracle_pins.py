@@ -1,0 +1,240 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped set in
+an intersection, a wrong orientation test, a missing factor, a transposed
+operand) breaks at least one of them: brute force on dense matrices,
+textbook closed forms, the symmetric-data multiples of App. A.1.2, the AGM
+bound of Sec. 2.1, and invariance under relabelling.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import graphs as G
+
+
+def og(n, edges):
+    s, d = G.arrays(edges)
+    return oracle.Graph(n, s, d)
+
+
+# ------------------------------------------------------------ triangles
+
+@pytest.mark.parametrize("seed", range(12))
+def test_triangles_vs_trace_a3(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 64))
+    p = float(rng.choice([0.05, 0.2, 0.5, 0.9]))
+    e = G.random_graph(n, p, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    assert g.triangles() == G.bf_triangles(A)
+    assert g.triangles(nthreads=4) == G.bf_triangles(A)
+
+
+@pytest.mark.parametrize("n", range(1, 14))
+def test_triangles_complete(n):
+    assert og(n, G.complete(n)).triangles() == math.comb(n, 3)
+
+
+def test_triangles_zero_families():
+    rng = np.random.default_rng(7)
+    n, e = G.complete_multipartite(5, 7)                      # bipartite K_{5,7}
+    assert og(n, e).triangles() == 0
+    assert og(20, G.star(20)).triangles() == 0
+    assert og(40, G.random_tree(40, rng)).triangles() == 0
+    for k in (4, 6, 10, 5, 7):                                # even and odd cycles > 3
+        assert og(k, G.cycle(k)).triangles() == 0
+    assert og(10, G.petersen()).triangles() == 0
+    assert og(3, G.cycle(3)).triangles() == 1
+
+
+@pytest.mark.parametrize("n", [4, 5, 8, 13])
+def test_triangles_wheel(n):
+    assert og(n + 1, G.wheel(n)).triangles() == n
+
+
+@pytest.mark.parametrize("parts", [(1, 1, 1), (2, 2, 2), (2, 3, 4), (5, 1, 3)])
+def test_triangles_tripartite(parts):
+    n, e = G.complete_multipartite(*parts)
+    assert og(n, e).triangles() == parts[0] * parts[1] * parts[2]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_symmetric_multiple_and_agm(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(10, 60))
+    e = G.random_graph(n, 0.3, rng)
+    g = og(n, e)
+    t = g.triangles()
+    assert g.triangles(pruned=False) == 6 * t            # App. A.1.2: symmetric data gives a multiple
+    assert g.clique4(pruned=False) == 24 * g.clique4()
+    assert t <= g.m ** 1.5                               # Sec. 2.1: |out| <= N^{3/2}
+
+
+def test_agm_tight_on_complete():
+    # Sec. 2.1 example: K_sqrt(N) has Theta(N^{3/2}) triangles
+    for k in (10, 20, 40):
+        g = og(k, G.complete(k))
+        assert g.triangles() == math.comb(k, 3)
+        assert g.triangles() >= 0.1 * g.m ** 1.5
+
+
+# ------------------------------------------------------------ 4-cliques
+
+@pytest.mark.parametrize("seed", range(8))
+def test_clique4_vs_subset_enumeration(seed):
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(6, 30))
+    e = G.random_graph(n, float(rng.choice([0.3, 0.6, 0.85])), rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    assert g.clique4() == G.bf_clique4(A)
+    assert g.clique4(nthreads=3) == G.bf_clique4(A)
+
+
+@pytest.mark.parametrize("n", range(1, 12))
+def test_clique4_complete(n):
+    assert og(n, G.complete(n)).clique4() == math.comb(n, 4)
+
+
+@pytest.mark.parametrize("parts", [(2, 2, 2, 2), (1, 2, 3, 4), (3, 3, 1, 2)])
+def test_clique4_multipartite(parts):
+    n, e = G.complete_multipartite(*parts)
+    assert og(n, e).clique4() == int(np.prod(parts))
+
+
+def test_clique4_zero():
+    n, e = G.complete_multipartite(2, 2, 2)   # octahedron: triangles, no K4
+    g = og(n, e)
+    assert g.triangles() == 8 and g.clique4() == 0
+    assert og(10, G.petersen()).clique4() == 0
+
+
+# ------------------------------------------------------------ lollipop
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lollipop_vs_literal_join(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(4, 16))
+    e = G.random_graph(n, 0.5, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    assert g.lollipop() == G.bf_lollipop(A)
+    # closed form through per-vertex triangle counts: sum_x 2 t(x) d(x)
+    t = G.bf_vertex_triangles(A)
+    assert g.lollipop() == int((2 * t * A.sum(1)).sum())
+    assert g.lollipop_distinct() == G.bf_lollipop_distinct(A)
+    assert g.lollipop_distinct() == int((t * (A.sum(1) - 2)).sum())
+
+
+@pytest.mark.parametrize("n", range(3, 10))
+def test_lollipop_complete(n):
+    g = og(n, G.complete(n))
+    assert g.lollipop() == n * (n - 1) * (n - 2) * (n - 1)
+    assert g.lollipop_distinct() == n * math.comb(n - 1, 2) * (n - 3)
+
+
+def test_vertex_triangles():
+    rng = np.random.default_rng(5)
+    n = 40
+    e = G.random_graph(n, 0.4, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    verts = np.arange(n, dtype=np.uint32)
+    assert np.array_equal(g.vertex_triangles(verts), G.bf_vertex_triangles(A).astype(np.uint64))
+
+
+# ------------------------------------------------------------ induced subgraphs
+
+def test_induced_subgraph():
+    rng = np.random.default_rng(11)
+    n = 50
+    e = G.random_graph(n, 0.3, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    full = g.induced(np.arange(n, dtype=np.uint32))
+    assert full.triangles() == g.triangles() and full.clique4() == g.clique4()
+    for trial in range(5):
+        S = rng.choice(n, size=int(rng.integers(3, n)), replace=False)
+        sub = g.induced(np.concatenate([S, S[:3]]).astype(np.uint32))   # repeats are harmless
+        As = A[np.ix_(np.sort(S), np.sort(S))]
+        assert sub.triangles() == G.bf_triangles(As)
+        assert sub.clique4() == G.bf_clique4(As)
+        assert sub.lollipop() == G.bf_lollipop(As)
+    # a planted clique's vertex set
+    kk = n - 40
+    e2 = e + [(40 + i, 40 + j) for i in range(kk) for j in range(i + 1, kk)]
+    g2 = og(n, e2)
+    sub = g2.induced(np.arange(40, n, dtype=np.uint32))
+    assert sub.triangles() == math.comb(kk, 3) and sub.clique4() == math.comb(kk, 4)
+
+
+def test_induced_rejects_bad_id():
+    g = og(5, G.complete(5))
+    with pytest.raises(ValueError):
+        g.induced(np.array([1, 7], np.uint32))
+
+
+# ------------------------------------------------------------ invariances
+
+@pytest.mark.parametrize("seed", range(4))
+def test_relabel_invariance(seed):
+    rng = np.random.default_rng(400 + seed)
+    n = 45
+    e = G.random_graph(n, 0.35, rng)
+    perm = rng.permutation(n)
+    e2 = [(int(perm[a]), int(perm[b])) for a, b in e]
+    g1, g2 = og(n, e), og(n, e2)
+    for pat in ("triangle", "clique4", "lollipop", "lollipop_distinct"):
+        assert g1.count(pat) == g2.count(pat)
+
+
+def test_direction_loops_duplicates_ignored():
+    e = G.complete(6)
+    noisy = e + [(b, a) for a, b in e] + [(v, v) for v in range(6)] + e[:4]
+    assert og(6, noisy).triangles() == 20 and og(6, noisy).m == 15
+
+
+# ------------------------------------------------------------ canonical relation, order, layout
+
+def test_canon_matches_set_semantics():
+    rng = np.random.default_rng(9)
+    n = 300
+    s = rng.integers(0, n, 5000).astype(np.uint32)
+    d = rng.integers(0, n, 5000).astype(np.uint32)
+    a, b = oracle.canon(s, d, n)
+    ref = sorted({(min(x, y), max(x, y)) for x, y in zip(s.tolist(), d.tolist()) if x != y})
+    assert list(zip(a.tolist(), b.tolist())) == ref
+    with pytest.raises(ValueError):
+        oracle.canon(np.array([0, 300], np.uint32), np.array([1, 2], np.uint32), n)
+
+
+def test_degree_order():
+    rng = np.random.default_rng(3)
+    n = 80
+    e = G.random_graph(n, 0.1, rng)
+    A = G.adjacency(n, e)
+    deg = A.sum(1)
+    want = sorted(range(n), key=lambda v: (-deg[v], v))
+    assert og(n, e).degree_order().tolist() == want
+
+
+def test_layout_rule():
+    # Sec. 4.4: bitset when range <= tau * |S|
+    assert oracle.layout_is_bitset(np.arange(100, 356), 1)          # range 256, |S| 256
+    assert not oracle.layout_is_bitset(np.array([0, 1000]), 256)     # range 1001 > 512
+    assert oracle.layout_is_bitset(np.array([0, 511]), 256)          # range 512 <= 512
+    assert not oracle.layout_is_bitset(np.array([0, 512]), 256)      # range 513 > 512
+    assert not oracle.layout_is_bitset(np.arange(10), 0)             # tau 0: all uint
+    assert oracle.layout_is_bitset(np.array([0, 4_000_000_000]), 0xFFFFFFFF)
+    assert not oracle.layout_is_bitset(np.array([], np.uint32), 0xFFFFFFFF)
+
+
+def test_empty_graph():
+    g = og(5, [])
+    assert g.m == 0 and g.triangles() == 0 and g.clique4() == 0 and g.lollipop() == 0
+    g0 = oracle.Graph(0, np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    assert g0.triangles() == 0

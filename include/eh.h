@@ -141,6 +141,23 @@ eh_status eh_count_async(const eh_trie *trie, eh_pattern pattern, const eh_exec_
  * status word of the trie's last asynchronous counts (then clears it). */
 eh_status eh_count_status(const eh_trie *trie, void *stream);
 
+/* eh_count_info_get -- work-plan facts of a whole-graph count (builds the
+ * plan if needed): alg_bytes = the bytes the method must move in one pass
+ * (staged sets once per vertex; per intersection the stored layout's bytes
+ * of the other set, or 32 bytes per probe on the galloping side; 8 bytes per
+ * edge of offsets), the number of heavy (CTA) and light (warp) vertices, and
+ * the kernel launches one eh_count_async enqueues. */
+typedef struct {
+    double alg_bytes;
+    uint64_t n_heavy;
+    uint64_t n_light;
+    uint32_t kernel_launches;
+    uint32_t reserved;
+} eh_count_info;
+
+eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
+                            eh_count_info *out);
+
 /* eh_vertex_triangles -- t(x), the number of triangles containing x, for
  * every original id x (host array of n_vertices uint64). */
 eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint64_t *out_t);

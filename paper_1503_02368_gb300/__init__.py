@@ -1,0 +1,6 @@
+"""GB300 (sm_103a) pattern-count engine: generic worst-case optimal join
+over a device-resident trie of uint/bitset neighbour sets (EmptyHeaded,
+arXiv 1503.02368).  The Python layer only marshals arguments into the C ABI
+of ``libeh.so`` (declared in ``include/eh.h``)."""
+from .eh import (PATTERNS, EHError, Server, Trie, build_opts, exec_opts, lib,  # noqa: F401
+                 library_path)

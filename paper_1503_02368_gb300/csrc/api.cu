@@ -1,0 +1,190 @@
+// api.cu -- the whole-graph entry points of eh.h and shared runtime helpers.
+#include "eh_internal.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace {
+thread_local char g_err[1024] = "";
+
+enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2 };
+
+// scratch layout (unsigned long long words of eh_trie::d_scratch)
+enum { SC_T = 0, SC_S = 1, SC_CNT = 2 /* 2 words */, SC_K4 = 4, SC_CNT2 = 6 /* 2 words */ };
+
+// result of a pattern from the accumulators: T (triangles), S (sum over
+// triangles of the three degrees), K (4-cliques)
+__global__ void k_finalize(const unsigned long long *acc, int pattern, unsigned long long *out, uint32_t *status) {
+    unsigned long long T = acc[SC_T], S = acc[SC_S], r = 0;
+    switch (pattern) {
+        case EH_TRIANGLE: r = T; break;
+        case EH_CLIQUE4: r = acc[SC_K4]; break;
+        case EH_LOLLIPOP:
+            if (S >> 63) atomicOr(status, DEV_ST_OVERFLOW);
+            r = 2ull * S;
+            break;
+        case EH_LOLLIPOP_DISTINCT: r = S - 6ull * T; break;
+    }
+    *out = r;
+}
+
+__global__ void k_vt_to_old(const unsigned long long *vt, const uint32_t *new2old, uint32_t n, unsigned long long *out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[new2old[i]] = vt[i];
+}
+
+eh_status check_status(eh_trie *t, cudaStream_t s) {
+    uint32_t st = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&st, t->d_status, 4, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) EH_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, 4, s));
+    if (st & DEV_ST_TIMEOUT) { eh_set_error("a bounded device wait timed out"); return EH_ETIMEOUT; }
+    if (st & DEV_ST_OVERFLOW) { eh_set_error("count exceeds uint64"); return EH_EOVERFLOW; }
+    if (st & DEV_ST_INVALID) { eh_set_error("invalid id on the device"); return EH_EINVAL; }
+    return EH_OK;
+}
+
+// enqueue one whole-graph count; result left in d_out (device)
+eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
+                        unsigned long long *d_out) {
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
+    unsigned long long *sc = t->d_scratch;
+    EH_CUDA_TRY(cudaMemsetAsync(sc, 0, 8 * sizeof(unsigned long long), s));
+    if (pattern == EH_CLIQUE4) {
+        EH_TRY(eh_launch_clique4(t, *plan, t->view(), xo, s, sc + SC_K4, sc + SC_CNT2, t->d_status, nullptr, 0));
+    } else {
+        int mode = pattern == EH_TRIANGLE ? M_COUNT : M_LOLLI;
+        EH_TRY(eh_launch_triangle(t, *plan, t->view(), mode, xo, s, sc + SC_T, sc + SC_CNT, t->d_status, nullptr,
+                                  nullptr));
+    }
+    k_finalize<<<1, 1, 0, s>>>(sc, (int)pattern, d_out, t->d_status);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
+}
+
+bool valid_pattern(int p) { return p >= EH_TRIANGLE && p <= EH_LOLLIPOP_DISTINCT; }
+
+}  // namespace
+
+void eh_set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char *eh_last_error(void) { return g_err; }
+
+int eh_num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = 1;
+        }
+    }
+    return sms;
+}
+
+eh_exec_opts eh_exec_defaults(const eh_exec_opts *x) {
+    eh_exec_opts o;
+    o.gallop_ratio = 32;
+    o.light_max = 32;
+    o.cta_warps = 8;
+    o.flags = 0;
+    if (x) {
+        if (x->gallop_ratio) o.gallop_ratio = x->gallop_ratio;
+        if (x->light_max) o.light_max = std::min<uint32_t>(x->light_max, 32u);
+        if (x->cta_warps == 4 || x->cta_warps == 8 || x->cta_warps == 16) o.cta_warps = x->cta_warps;
+        o.flags = x->flags;
+    }
+    return o;
+}
+
+eh_status eh_count_subset(const eh_trie *trie, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
+                          const eh_exec_opts *xopts, void *stream, uint64_t *out_count);
+
+extern "C" eh_status eh_count_ex(const eh_trie *trie, eh_pattern pattern, const uint32_t *subset,
+                                 uint32_t subset_len, const eh_exec_opts *xopts, void *stream, uint64_t *out_count) {
+    if (!trie || !out_count) { eh_set_error("eh_count: NULL argument"); return EH_EINVAL; }
+    if (!valid_pattern(pattern)) { eh_set_error("eh_count: unknown pattern %d", (int)pattern); return EH_EINVAL; }
+    if (subset && subset_len) return eh_count_subset(trie, pattern, subset, subset_len, xopts, stream, out_count);
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    cudaStream_t s = (cudaStream_t)stream;
+    eh_exec_opts xo = eh_exec_defaults(xopts);
+    std::lock_guard<std::mutex> g(t->call_mu);
+    unsigned long long *d_out = t->d_scratch + 15;
+    EH_TRY(enqueue_count(t, pattern, xo, s, d_out));
+    unsigned long long r = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&r, d_out, 8, cudaMemcpyDeviceToHost, s));
+    EH_TRY(check_status(t, s));
+    *out_count = r;
+    return EH_OK;
+}
+
+extern "C" eh_status eh_count(const eh_trie *trie, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
+                              void *stream, uint64_t *out_count) {
+    return eh_count_ex(trie, pattern, subset, subset_len, nullptr, stream, out_count);
+}
+
+extern "C" eh_status eh_count_async(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts,
+                                    void *stream, uint64_t *d_out_count) {
+    if (!trie || !d_out_count) { eh_set_error("eh_count_async: NULL argument"); return EH_EINVAL; }
+    if (!valid_pattern(pattern)) { eh_set_error("eh_count_async: unknown pattern %d", (int)pattern); return EH_EINVAL; }
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    eh_exec_opts xo = eh_exec_defaults(xopts);
+    return enqueue_count(t, pattern, xo, (cudaStream_t)stream, (unsigned long long *)d_out_count);
+}
+
+extern "C" eh_status eh_count_status(const eh_trie *trie, void *stream) {
+    if (!trie) { eh_set_error("eh_count_status: NULL trie"); return EH_EINVAL; }
+    return check_status(const_cast<eh_trie *>(trie), (cudaStream_t)stream);
+}
+
+extern "C" eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts,
+                                       void *stream, eh_count_info *out) {
+    if (!trie || !out) { eh_set_error("eh_count_info_get: NULL argument"); return EH_EINVAL; }
+    if (!valid_pattern(pattern)) { eh_set_error("eh_count_info_get: unknown pattern"); return EH_EINVAL; }
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    eh_exec_opts xo = eh_exec_defaults(xopts);
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, (cudaStream_t)stream, &plan));
+    memset(out, 0, sizeof(*out));
+    out->alg_bytes = pattern == EH_CLIQUE4 ? plan->alg_bytes_k4 : plan->alg_bytes;
+    out->n_heavy = plan->n_heavy;
+    out->n_light = plan->n_light;
+    out->kernel_launches = 2;   // the count kernel and the finalize kernel
+    return EH_OK;
+}
+
+extern "C" eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint64_t *out_t) {
+    if (!trie || !out_t) { eh_set_error("eh_vertex_triangles: NULL argument"); return EH_EINVAL; }
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    cudaStream_t s = (cudaStream_t)stream;
+    eh_exec_opts xo = eh_exec_defaults(nullptr);
+    std::lock_guard<std::mutex> g(t->call_mu);
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
+    unsigned long long *vt = nullptr, *vo = nullptr;
+    EH_TRY(dev_alloc(&vt, t->n, s));
+    eh_status st = dev_alloc(&vo, t->n, s);
+    if (st == EH_OK) {
+        cudaMemsetAsync(vt, 0, (uint64_t)t->n * 8, s);
+        cudaMemsetAsync(t->d_scratch, 0, 8 * sizeof(unsigned long long), s);
+        st = eh_launch_triangle(t, *plan, t->view(), M_VERTEX, xo, s, t->d_scratch + SC_T, t->d_scratch + SC_CNT,
+                                t->d_status, vt, nullptr);
+    }
+    if (st == EH_OK && t->n) {
+        k_vt_to_old<<<(t->n + 255) / 256, 256, 0, s>>>(vt, t->d_new2old, t->n, vo);
+        cudaError_t e = cudaMemcpyAsync(out_t, vo, (uint64_t)t->n * 8, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) { eh_set_error("eh_vertex_triangles: %s", cudaGetErrorString(e)); st = EH_ECUDA; }
+    }
+    if (st == EH_OK) st = check_status(t, s);
+    dev_free(vt, s);
+    dev_free(vo, s);
+    cudaStreamSynchronize(s);
+    return st;
+}

@@ -1,0 +1,778 @@
+// count.cu -- the intersection kernels of the pattern counts.
+//
+// Triangle (EmptyHeaded Sec. 3.3.2 loop nest, on the degree-pruned trie of
+// App. A.1.2):  T = sum_u sum_{v in N+(u)} |N+(u) ∩ N+(v)|.
+// For u, the set A = N+(u) is staged once on chip and reused by every v.
+// Because N+(v) ⊂ [0, v) and A is sorted, only the prefix A_<v = A[0..j) of
+// A (v = A[j]) can meet N+(v); every intersection below works on that prefix.
+//
+// Each intersection A ∩ B, B = N+(v), picks its algorithm from the layout
+// pair and the sizes, as the paper's execution engine does (Sec. 4.2):
+//   A bitmap  ∩ B bitset : 128-bit AND of the overlapping words + popc      (bitset ∩ bitset)
+//   A bitmap  ∩ B uint   : each element of B probes one bit of A            (uint ∩ bitset)
+//   A sorted  ∩ B bitset : each element of A_<v probes one bit of B         (uint ∩ bitset)
+//   A sorted  ∩ B uint   : |B| > ratio*|A_<v| -> binary search of A_<v in B (galloping side)
+//                          otherwise          -> B streamed in 128-element chunks against
+//                                                the window of A_<v the chunk spans (merge)
+// A is a bitmap when its stored layout is a bitset, or when its value range
+// fits the CTA's shared-memory budget (an on-chip re-encoding of the stored
+// uint array).  Work is split by degree: vertices with |N+(u)| > light_max get
+// a whole CTA whose warps share the staged A and take the v's dynamically;
+// lighter ones get one warp each, A held one element per lane.
+#include "eh_internal.cuh"
+
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr uint32_t BM_CAP_WORDS = 8192;        // 32 KB on-chip bitmap: value ranges up to 262,144
+constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 22; // bounded wait for a bulk copy
+
+enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2 };
+
+struct Acc {
+    unsigned long long t;   // triangles
+    unsigned long long s;   // sum over triangles of d(a)+d(b)+d(c)  (lollipop)
+};
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------- bulk copy (TMA)
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion counted on mbar (bytes % 16 == 0,
+// both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// returns true when the phase with the given parity completed within the limit
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < MBAR_SPIN_LIMIT && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
+// --------------------------------------------------------------- matches
+
+template <int MODE>
+__device__ __forceinline__ void on_match(Acc &acc, uint32_t w, uint32_t duv, const TrieView &tv,
+                                         unsigned long long *vt) {
+    acc.t += 1;
+    if (MODE == M_LOLLI) acc.s += duv + __ldg(&tv.deg[w]);
+    if (MODE == M_VERTEX) atomicAdd(&vt[w], 1ull);
+}
+
+// all set bits of x (value base + bit) are matches
+template <int MODE>
+__device__ __forceinline__ void on_word(Acc &acc, uint32_t x, uint32_t base, uint32_t duv, const TrieView &tv,
+                                        unsigned long long *vt) {
+    if (MODE == M_COUNT) {
+        acc.t += __popc(x);
+    } else {
+        while (x) {
+            uint32_t b = __ffs(x) - 1;
+            x &= x - 1;
+            on_match<MODE>(acc, base + b, duv, tv, vt);
+        }
+    }
+}
+
+// ------------------------------------------------------ per-pair routines
+
+// A bitmap (shared memory, words [a_lo, a_lo+a_nw)) ∩ B
+template <int MODE>
+__device__ __forceinline__ void pair_bitmap(const TrieView &tv, const uint32_t *sA, uint32_t a_lo, uint32_t a_nw,
+                                            const SetDesc &dv, uint32_t duv, Acc &acc, unsigned long long *vt) {
+    const int lane = threadIdx.x & 31;
+    if (dv.nwords) {
+        uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
+        uint32_t ov = hi > lo ? hi - lo : 0;
+        if (ov <= dv.len) {   // fewer words than elements: bitset ∩ bitset
+            const uint32_t *bw = tv.words + dv.woff - dv.lo_word;
+            for (uint32_t i = lo + lane * 4; i < hi; i += 128) {
+                uint4 b = ldg4(bw + i);
+                uint4 a = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
+                on_word<MODE>(acc, a.x & b.x, i * 32, duv, tv, vt);
+                on_word<MODE>(acc, a.y & b.y, i * 32 + 32, duv, tv, vt);
+                on_word<MODE>(acc, a.z & b.z, i * 32 + 64, duv, tv, vt);
+                on_word<MODE>(acc, a.w & b.w, i * 32 + 96, duv, tv, vt);
+            }
+            return;
+        }
+    }
+    // uint B: each element probes A's bitmap (padding EH_PAD is out of range)
+    const uint32_t *bp = tv.nbr + dv.off;
+    const uint32_t base = a_lo * 32, nbits = a_nw * 32;
+    for (uint32_t p = lane * 4; p < dv.len; p += 128) {
+        uint4 e = ldg4(bp + p);
+        uint32_t w[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t x = w[c] - base;
+            if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) on_match<MODE>(acc, w[c], duv, tv, vt);
+        }
+    }
+}
+
+// smallest index i in [lo, hi) with A[i] >= key (A sorted), or hi
+__device__ __forceinline__ uint32_t lower_bound(const uint32_t *A, uint32_t lo, uint32_t hi, uint32_t key) {
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (A[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// A sorted array (shared or global), effective prefix A[0..j) ∩ B
+template <int MODE>
+__device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *A, uint32_t j, const SetDesc &dv,
+                                            uint32_t duv, uint32_t ratio, Acc &acc, unsigned long long *vt) {
+    const int lane = threadIdx.x & 31;
+    if (dv.nwords && j <= dv.len) {   // uint ∩ bitset: probe A's elements
+        const uint32_t *bw = tv.words + dv.woff;
+        const uint32_t base = dv.lo_word * 32, nbits = dv.nwords * 32;
+        for (uint32_t i = lane; i < j; i += 32) {
+            uint32_t a = A[i], x = a - base;
+            if (x < nbits && ((__ldg(&bw[x >> 5]) >> (x & 31)) & 1u)) on_match<MODE>(acc, a, duv, tv, vt);
+        }
+        return;
+    }
+    const uint32_t *B = tv.nbr + dv.off;
+    if ((uint64_t)dv.len > (uint64_t)ratio * j) {   // galloping side: search A's elements in B
+        for (uint32_t i = lane; i < j; i += 32) {
+            uint32_t a = A[i];
+            uint32_t pos = lower_bound(B, 0, dv.len, a);
+            if (pos < dv.len && __ldg(&B[pos]) == a) on_match<MODE>(acc, a, duv, tv, vt);
+        }
+        return;
+    }
+    // merge side: B in 128-element chunks; each chunk meets the window of A it spans
+    uint32_t wlo = 0;
+    for (uint32_t c = 0; c < dv.len; c += 128) {
+        uint32_t p = c + lane * 4;
+        uint4 e = p < dv.len ? ldg4(B + p) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+        uint32_t bmin = __shfl_sync(FULL, e.x, 0);
+        uint32_t mx = e.w != EH_PAD ? e.w : e.z != EH_PAD ? e.z : e.y != EH_PAD ? e.y : e.x != EH_PAD ? e.x : 0u;
+        uint32_t bmax = __reduce_max_sync(FULL, mx);
+        uint32_t lo = 0, hi = 0;
+        if (lane == 0) lo = lower_bound(A, wlo, j, bmin);
+        if (lane == 1) hi = lower_bound(A, wlo, j, bmax + 1);
+        lo = __shfl_sync(FULL, lo, 0);
+        hi = __shfl_sync(FULL, hi, 1);
+        wlo = lo;
+        if (hi <= lo) continue;
+        uint32_t w[4] = {e.x, e.y, e.z, e.w};
+        if (hi - lo <= 8) {
+            for (uint32_t i = lo; i < hi; ++i) {
+                uint32_t a = A[i];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (w[k] == a) on_match<MODE>(acc, a, duv, tv, vt);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (w[k] == EH_PAD) continue;
+                uint32_t pos = lower_bound(A, lo, hi, w[k]);
+                if (pos < hi && A[pos] == w[k]) on_match<MODE>(acc, w[k], duv, tv, vt);
+            }
+        }
+    }
+}
+
+// A held one element per lane (lanes < eff active, sorted): is the lane's
+// element in B?  The algorithm follows the layout pair and the sizes.
+__device__ __forceinline__ bool light_match(const TrieView &tv, uint32_t a, uint32_t eff, const SetDesc &dB,
+                                            uint32_t ratio) {
+    const int lane = threadIdx.x & 31;
+    const bool act = (uint32_t)lane < eff;
+    if (dB.nwords && eff <= dB.len) {   // uint ∩ bitset: probe one bit
+        uint32_t x = a - dB.lo_word * 32;
+        return act && x < dB.nwords * 32 && ((__ldg(&tv.words[dB.woff + (x >> 5)]) >> (x & 31)) & 1u);
+    }
+    const uint32_t *B = tv.nbr + dB.off;
+    if ((uint64_t)dB.len > (uint64_t)ratio * eff) {   // galloping side: binary search in B
+        if (!act) return false;
+        uint32_t pos = lower_bound(B, 0, dB.len, a);
+        return pos < dB.len && __ldg(&B[pos]) == a;
+    }
+    // merge side: B in 128-element chunks against the lanes whose value falls in the chunk's span
+    bool hit = false;
+    for (uint32_t c = 0; c < dB.len; c += 128) {
+        uint32_t p = c + lane * 4;
+        uint4 e = p < dB.len ? ldg4(B + p) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+        uint32_t bmin = __shfl_sync(FULL, e.x, 0);
+        uint32_t mx = e.w != EH_PAD ? e.w : e.z != EH_PAD ? e.z : e.y != EH_PAD ? e.y : e.x != EH_PAD ? e.x : 0u;
+        uint32_t bmax = __reduce_max_sync(FULL, mx);
+        uint32_t win = __ballot_sync(FULL, act && a >= bmin && a <= bmax);
+        while (win) {
+            uint32_t i = __ffs(win) - 1;
+            win &= win - 1;
+            uint32_t ai = __shfl_sync(FULL, a, i);
+            bool any = __any_sync(FULL, e.x == ai || e.y == ai || e.z == ai || e.w == ai);
+            if (any && (uint32_t)lane == i) hit = true;
+        }
+    }
+    return hit;
+}
+
+// light vertex: A = N+(u) (2 <= |A| <= 32) one element per lane
+template <int MODE>
+__device__ void light_vertex(const TrieView &tv, uint32_t u, uint32_t ratio, Acc &acc, unsigned long long *vt) {
+    const int lane = threadIdx.x & 31;
+    const SetDesc du = tv.desc[u];
+    const uint32_t k = du.len;
+    const uint32_t a = lane < k ? __ldg(&tv.nbr[du.off + lane]) : EH_PAD;
+    for (uint32_t j = 1; j < k; ++j) {
+        const uint32_t v = __shfl_sync(FULL, a, j);
+        const SetDesc dv = tv.desc[v];
+        if (dv.len == 0) continue;
+        const bool hit = light_match(tv, a, j, dv, ratio);
+        if (hit) on_match<MODE>(acc, a, du.deg + dv.deg, tv, vt);
+        if (MODE == M_VERTEX) {
+            uint32_t pc = __popc(__ballot_sync(FULL, hit));
+            if (lane == 0 && pc) {
+                atomicAdd(&vt[u], (unsigned long long)pc);
+                atomicAdd(&vt[v], (unsigned long long)pc);
+            }
+        }
+    }
+}
+
+// counters[0]: next heavy item, counters[1]: next light chunk
+template <int MODE, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint32_t *__restrict__ heavy, uint32_t n_heavy,
+                                                         const uint32_t *__restrict__ light, uint32_t n_light,
+                                                         uint32_t ratio, unsigned long long *counters,
+                                                         unsigned long long *out, uint32_t *status,
+                                                         unsigned long long *vt) {
+    extern __shared__ __align__(16) uint32_t sA[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_item, s_next;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Acc acc{0, 0};
+    uint32_t phase = 0;
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+
+    // heavy vertices: one CTA each
+    for (;;) {
+        if (tid == 0) s_item = (uint32_t)min((unsigned long long)n_heavy, atomicAdd(&counters[0], 1ull));
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_heavy) break;
+        const uint32_t u = heavy[item];
+        const SetDesc du = tv.desc[u];
+        const uint32_t len = du.len;
+        const uint32_t *Ag = tv.nbr + du.off;
+        const uint32_t first = __ldg(&Ag[0]), last = __ldg(&Ag[len - 1]);
+        // on-chip form of A
+        uint32_t a_lo = (first >> 7) << 2;
+        uint32_t a_nw = (((last >> 5) + 1 - a_lo) + 3) & ~3u;
+        int amode;   // 0 bitmap, 1 sorted in shared memory, 2 sorted in global memory
+        if (du.nwords && du.nwords <= BM_CAP_WORDS) {
+            amode = 0;
+            a_lo = du.lo_word;
+            a_nw = du.nwords;
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&mbar, a_nw * 4);
+                bulk_g2s(sA, tv.words + du.woff, a_nw * 4, &mbar);
+            }
+        } else if (a_nw <= BM_CAP_WORDS) {
+            amode = 0;
+            for (uint32_t i = tid * 4; i < a_nw; i += WARPS * 128)
+                *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            for (uint32_t i = tid; i < len; i += WARPS * 32) {
+                uint32_t x = __ldg(&Ag[i]);
+                atomicOr(&sA[(x >> 5) - a_lo], 1u << (x & 31));
+            }
+        } else if (len <= BM_CAP_WORDS) {
+            amode = 1;
+            if (tid == 0) {
+                uint32_t bytes = ((len + 3) & ~3u) * 4;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&mbar, bytes);
+                bulk_g2s(sA, Ag, bytes, &mbar);
+            }
+        } else {
+            amode = 2;
+        }
+        if (tid == 0) s_next = 1;
+        if ((du.nwords && du.nwords <= BM_CAP_WORDS) || amode == 1) {
+            bool ok = mbar_wait(&mbar, phase);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
+                mbar_wait(&mbar, phase ^ 1);   // drain the copy still in flight, bounded
+                return;
+            }
+        } else {
+            __syncthreads();
+        }
+        const uint32_t *A = amode == 2 ? Ag : sA;
+        for (;;) {
+            uint32_t j = 0;
+            if (lane == 0) j = atomicAdd(&s_next, 1u);
+            j = __shfl_sync(FULL, j, 0);
+            if (j >= len) break;
+            const uint32_t v = amode == 0 ? __ldg(&Ag[j]) : A[j];
+            const SetDesc dv = tv.desc[v];
+            if (dv.len == 0) continue;
+            const uint32_t duv = du.deg + dv.deg;
+            unsigned long long t0 = acc.t;
+            if (amode == 0) pair_bitmap<MODE>(tv, sA, a_lo, a_nw, dv, duv, acc, vt);
+            else pair_sorted<MODE>(tv, A, j, dv, duv, ratio, acc, vt);
+            if (MODE == M_VERTEX) {
+                unsigned long long pc = acc.t - t0;
+                for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
+                if (lane == 0 && pc) {
+                    atomicAdd(&vt[u], pc);
+                    atomicAdd(&vt[v], pc);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // light vertices: one warp each, taken 32 at a time
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&counters[1], 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= n_light) break;
+        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
+        for (uint32_t i = (uint32_t)base; i < end; ++i) light_vertex<MODE>(tv, __ldg(&light[i]), ratio, acc, vt);
+    }
+
+    // reduce: warp, then one atomic per warp
+    unsigned long long t = acc.t, s = acc.s;
+    for (int d = 16; d > 0; d >>= 1) {
+        t += __shfl_xor_sync(FULL, t, d);
+        s += __shfl_xor_sync(FULL, s, d);
+    }
+    if (lane == 0) {
+        if (t) atomicAdd(&out[0], t);
+        if (MODE == M_LOLLI && s) {
+            unsigned long long old = atomicAdd(&out[1], s);
+            if (old + s < old) atomicOr(status, DEV_ST_OVERFLOW);
+        }
+    }
+    (void)warp;
+}
+
+
+// ------------------------------------------------------------------ 4-clique
+//
+// Table 1's 4Clique on the pruned trie with the attribute order x > y > z > w
+// (a single-node GHD is optimal for it, Sec. 5.2.2):
+//   for x; for y in N+(x): S = N+(x) ∩ N+(y) (materialised, sorted);
+//     for z in S: K4 += |S_<z ∩ N+(z)|.
+// Level 1 writes S by warp compaction (ballot / scan of per-lane match
+// counts, in increasing order) into a per-warp shared buffer, or into the
+// warp's slice of a global arena when |S| may exceed it.  Level 2 runs the
+// same layout-dispatched intersection as the triangle on (S_<z, N+(z)).
+
+constexpr uint32_t S_CAP = 1024;   // per-warp shared S buffer (elements)
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t &total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    total = __shfl_sync(FULL, incl, 31);
+    return incl - x;
+}
+
+// S = A ∩ B, A an on-chip bitmap
+__device__ uint32_t emit_bitmap(const TrieView &tv, const uint32_t *sA, uint32_t a_lo, uint32_t a_nw,
+                                const SetDesc &dv, uint32_t *S) {
+    const int lane = threadIdx.x & 31;
+    uint32_t ns = 0;
+    if (dv.nwords) {
+        uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
+        uint32_t ov = hi > lo ? hi - lo : 0;
+        if (ov <= dv.len) {
+            const uint32_t *bw = tv.words + dv.woff - dv.lo_word;
+            for (uint32_t b0 = lo; b0 < hi; b0 += 128) {
+                uint32_t i = b0 + lane * 4;
+                uint32_t x[4] = {0, 0, 0, 0};
+                if (i < hi) {
+                    uint4 b = ldg4(bw + i);
+                    uint4 a = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
+                    x[0] = a.x & b.x; x[1] = a.y & b.y; x[2] = a.z & b.z; x[3] = a.w & b.w;
+                }
+                uint32_t cnt = __popc(x[0]) + __popc(x[1]) + __popc(x[2]) + __popc(x[3]), tot;
+                uint32_t pos = ns + warp_excl_scan(cnt, tot);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t w = x[k];
+                    while (w) {
+                        uint32_t bb = __ffs(w) - 1;
+                        w &= w - 1;
+                        S[pos++] = (i + k) * 32 + bb;
+                    }
+                }
+                ns += tot;
+            }
+            __syncwarp();
+            return ns;
+        }
+    }
+    const uint32_t *bp = tv.nbr + dv.off;
+    const uint32_t base = a_lo * 32, nbits = a_nw * 32;
+    for (uint32_t c = 0; c < dv.len; c += 128) {
+        uint32_t p = c + lane * 4;
+        uint4 e = p < dv.len ? ldg4(bp + p) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+        uint32_t w[4] = {e.x, e.y, e.z, e.w};
+        uint32_t f = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = w[k] - base;
+            if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) f |= 1u << k;
+        }
+        uint32_t tot;
+        uint32_t pos = ns + warp_excl_scan(__popc(f), tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (f & (1u << k)) S[pos++] = w[k];
+        ns += tot;
+    }
+    __syncwarp();
+    return ns;
+}
+
+// S = A[0..j) ∩ B, A sorted (shared or global)
+__device__ uint32_t emit_sorted(const TrieView &tv, const uint32_t *A, uint32_t j, const SetDesc &dv, uint32_t ratio,
+                                uint32_t *S) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t ns = 0;
+    const uint32_t *B = tv.nbr + dv.off;
+    const bool probe = dv.nwords && j <= dv.len;
+    if (probe || (uint64_t)dv.len > (uint64_t)ratio * j) {
+        const uint32_t base = dv.lo_word * 32, nbits = dv.nwords * 32;
+        for (uint32_t r = 0; r < j; r += 32) {
+            uint32_t i = r + lane;
+            bool hit = false;
+            uint32_t a = 0;
+            if (i < j) {
+                a = A[i];
+                if (probe) {
+                    uint32_t x = a - base;
+                    hit = x < nbits && ((__ldg(&tv.words[dv.woff + (x >> 5)]) >> (x & 31)) & 1u);
+                } else {
+                    uint32_t pos = lower_bound(B, 0, dv.len, a);
+                    hit = pos < dv.len && __ldg(&B[pos]) == a;
+                }
+            }
+            uint32_t m = __ballot_sync(FULL, hit);
+            if (hit) S[ns + __popc(m & lt)] = a;
+            ns += __popc(m);
+        }
+        __syncwarp();
+        return ns;
+    }
+    uint32_t wlo = 0;
+    for (uint32_t c = 0; c < dv.len; c += 128) {
+        uint32_t p = c + lane * 4;
+        uint4 e = p < dv.len ? ldg4(B + p) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+        uint32_t bmin = __shfl_sync(FULL, e.x, 0);
+        uint32_t mx = e.w != EH_PAD ? e.w : e.z != EH_PAD ? e.z : e.y != EH_PAD ? e.y : e.x != EH_PAD ? e.x : 0u;
+        uint32_t bmax = __reduce_max_sync(FULL, mx);
+        uint32_t lo = 0, hi = 0;
+        if (lane == 0) lo = lower_bound(A, wlo, j, bmin);
+        if (lane == 1) hi = lower_bound(A, wlo, j, bmax + 1);
+        lo = __shfl_sync(FULL, lo, 0);
+        hi = __shfl_sync(FULL, hi, 1);
+        wlo = lo;
+        uint32_t w[4] = {e.x, e.y, e.z, e.w};
+        uint32_t f = 0;
+        if (hi > lo) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (w[k] == EH_PAD) continue;
+                uint32_t pos = lower_bound(A, lo, hi, w[k]);
+                if (pos < hi && A[pos] == w[k]) f |= 1u << k;
+            }
+        }
+        uint32_t tot;
+        uint32_t pos = ns + warp_excl_scan(__popc(f), tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (f & (1u << k)) S[pos++] = w[k];
+        ns += tot;
+    }
+    __syncwarp();
+    return ns;
+}
+
+// level 2 over a materialised sorted S
+__device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t *S, uint32_t ns, uint32_t ratio,
+                                              Acc &acc) {
+    for (uint32_t i = 1; i < ns; ++i) {
+        const uint32_t z = S[i];
+        const SetDesc dz = tv.desc[z];
+        if (dz.len == 0) continue;
+        pair_sorted<M_COUNT>(tv, S, i, dz, 0, ratio, acc, nullptr);
+    }
+}
+
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
+    for (uint32_t k = 0; k < r; ++k) m &= m - 1;
+    return m ? (uint32_t)(__ffs(m) - 1) : 0u;
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint32_t *__restrict__ heavy, uint32_t n_heavy,
+                                                        const uint32_t *__restrict__ light, uint32_t n_light,
+                                                        uint32_t ratio, unsigned long long *counters,
+                                                        unsigned long long *out, uint32_t *status, uint32_t *arena,
+                                                        uint64_t arena_per_warp) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *sA = smem;
+    uint32_t *sS = smem + BM_CAP_WORDS;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_item, s_next;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
+    Acc acc{0, 0};
+    uint32_t phase = 0;
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) s_item = (uint32_t)min((unsigned long long)n_heavy, atomicAdd(&counters[0], 1ull));
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_heavy) break;
+        const uint32_t x = heavy[item];
+        const SetDesc dx = tv.desc[x];
+        const uint32_t len = dx.len;
+        const uint32_t *Ag = tv.nbr + dx.off;
+        const uint32_t first = __ldg(&Ag[0]), last = __ldg(&Ag[len - 1]);
+        uint32_t a_lo = (first >> 7) << 2;
+        uint32_t a_nw = (((last >> 5) + 1 - a_lo) + 3) & ~3u;
+        int amode;
+        bool copy = false;
+        if (dx.nwords && dx.nwords <= BM_CAP_WORDS) {
+            amode = 0;
+            a_lo = dx.lo_word;
+            a_nw = dx.nwords;
+            copy = true;
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&mbar, a_nw * 4);
+                bulk_g2s(sA, tv.words + dx.woff, a_nw * 4, &mbar);
+            }
+        } else if (a_nw <= BM_CAP_WORDS) {
+            amode = 0;
+            for (uint32_t i = tid * 4; i < a_nw; i += WARPS * 128)
+                *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            for (uint32_t i = tid; i < len; i += WARPS * 32) {
+                uint32_t v = __ldg(&Ag[i]);
+                atomicOr(&sA[(v >> 5) - a_lo], 1u << (v & 31));
+            }
+        } else if (len <= BM_CAP_WORDS) {
+            amode = 1;
+            copy = true;
+            if (tid == 0) {
+                uint32_t bytes = ((len + 3) & ~3u) * 4;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&mbar, bytes);
+                bulk_g2s(sA, Ag, bytes, &mbar);
+            }
+        } else {
+            amode = 2;
+        }
+        if (tid == 0) s_next = 2;
+        if (copy) {
+            bool ok = mbar_wait(&mbar, phase);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
+                mbar_wait(&mbar, phase ^ 1);
+                return;
+            }
+        } else {
+            __syncthreads();
+        }
+        const uint32_t *A = amode == 2 ? Ag : sA;
+        for (;;) {
+            uint32_t j = 0;
+            if (lane == 0) j = atomicAdd(&s_next, 1u);
+            j = __shfl_sync(FULL, j, 0);
+            if (j >= len) break;
+            const uint32_t y = amode == 0 ? __ldg(&Ag[j]) : A[j];
+            const SetDesc dy = tv.desc[y];
+            if (dy.len < 2) continue;
+            const uint32_t bound = min(j, dy.len);
+            uint32_t *S = bound <= S_CAP ? sS + warp * S_CAP : arena + gwarp * arena_per_warp;
+            if (bound > S_CAP && (arena == nullptr || bound > arena_per_warp)) {
+                if (lane == 0) atomicOr(status, DEV_ST_INVALID);
+                continue;
+            }
+            uint32_t ns = amode == 0 ? emit_bitmap(tv, sA, a_lo, a_nw, dy, S) : emit_sorted(tv, A, j, dy, ratio, S);
+            clique_level2(tv, S, ns, ratio, acc);
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+
+    // light vertices: A and S held one element per lane
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&counters[1], 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= n_light) break;
+        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
+        for (uint32_t it = (uint32_t)base; it < end; ++it) {
+            const uint32_t x = __ldg(&light[it]);
+            const SetDesc dx = tv.desc[x];
+            const uint32_t k = dx.len;
+            const uint32_t a = lane < k ? __ldg(&tv.nbr[dx.off + lane]) : EH_PAD;
+            for (uint32_t j = 2; j < k; ++j) {
+                const uint32_t y = __shfl_sync(FULL, a, j);
+                const SetDesc dy = tv.desc[y];
+                if (dy.len < 2) continue;
+                const uint32_t m = __ballot_sync(FULL, light_match(tv, a, j, dy, ratio));
+                const uint32_t ns = __popc(m);
+                if (ns < 2) continue;
+                const uint32_t src = (uint32_t)lane < ns ? nth_set_bit(m, lane) : 0u;
+                uint32_t sv = __shfl_sync(FULL, a, src);
+                if ((uint32_t)lane >= ns) sv = EH_PAD;
+                for (uint32_t i = 1; i < ns; ++i) {
+                    const uint32_t z = __shfl_sync(FULL, sv, i);
+                    const SetDesc dz = tv.desc[z];
+                    if (dz.len == 0) continue;
+                    if (light_match(tv, sv, i, dz, ratio)) acc.t += 1;
+                }
+            }
+        }
+    }
+
+    unsigned long long t = acc.t;
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
+    if (lane == 0 && t) atomicAdd(&out[0], t);
+}
+
+template <int WARPS>
+eh_status launch_k4(eh_trie *t, const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
+                    unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status) {
+    auto kern = k_clique4<WARPS>;
+    const int smem = (BM_CAP_WORDS + WARPS * S_CAP) * 4;
+    EH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)(eh_num_sms() * per_sm);
+    uint64_t per_warp = ((uint64_t)t->max_out + 3) & ~3ull;
+    uint32_t *arena = nullptr;
+    if (t->max_out > S_CAP) {
+        std::lock_guard<std::mutex> g(t->mu);
+        uint64_t need = per_warp * grid * WARPS;
+        if (t->arena_words < need) {
+            cudaFree(t->d_arena);
+            t->d_arena = nullptr;
+            t->arena_words = 0;
+            EH_CUDA_TRY(cudaMalloc((void **)&t->d_arena, need * 4));
+            t->arena_words = need;
+        }
+        arena = t->d_arena;
+    }
+    EH_CUDA_TRY(cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned long long), s));
+    kern<<<grid, WARPS * 32, smem, s>>>(tv, plan.d_heavy, plan.n_heavy, plan.d_light, plan.n_light, xo.gallop_ratio,
+                                        d_counters, d_acc, d_status, arena, per_warp);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
+}
+
+template <int MODE, int WARPS>
+eh_status launch_tri(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
+                     unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status,
+                     unsigned long long *d_vt) {
+    auto kern = k_triangle<MODE, WARPS>;
+    const int smem = BM_CAP_WORDS * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        EH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = true;
+    }
+    int per_sm = 0;
+    EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)(eh_num_sms() * per_sm);
+    EH_CUDA_TRY(cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned long long), s));
+    kern<<<grid, WARPS * 32, smem, s>>>(tv, plan.d_heavy, plan.n_heavy, plan.d_light, plan.n_light,
+                                        xo.gallop_ratio, d_counters, d_acc, d_status, d_vt);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
+}
+
+template <int MODE>
+eh_status launch_tri_w(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
+                       unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status,
+                       unsigned long long *d_vt) {
+    switch (xo.cta_warps) {
+        case 4: return launch_tri<MODE, 4>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        case 16: return launch_tri<MODE, 16>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        default: return launch_tri<MODE, 8>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+    }
+}
+
+}  // namespace
+
+eh_status eh_launch_triangle(const eh_trie *t, const WorkPlan &plan, TrieView tv, int mode, const eh_exec_opts &xo,
+                             cudaStream_t s, unsigned long long *d_acc, unsigned long long *d_counters,
+                             uint32_t *d_status, unsigned long long *d_vt, const uint32_t *d_qid) {
+    (void)t;
+    (void)d_qid;
+    switch (mode) {
+        case M_COUNT: return launch_tri_w<M_COUNT>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        case M_LOLLI: return launch_tri_w<M_LOLLI>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        case M_VERTEX: return launch_tri_w<M_VERTEX>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+    }
+    eh_set_error("unknown triangle mode %d", mode);
+    return EH_EINVAL;
+}
+
+eh_status eh_launch_clique4(const eh_trie *t, const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo,
+                            cudaStream_t s, unsigned long long *d_acc, unsigned long long *d_counters,
+                            uint32_t *d_status, uint32_t *d_arena, uint64_t arena_words_per_warp) {
+    (void)d_arena;
+    (void)arena_words_per_warp;
+    eh_trie *tt = const_cast<eh_trie *>(t);
+    switch (xo.cta_warps) {
+        case 4: return launch_k4<4>(tt, plan, tv, xo, s, d_acc, d_counters, d_status);
+        case 16: return launch_k4<16>(tt, plan, tv, xo, s, d_acc, d_counters, d_status);
+        default: return launch_k4<8>(tt, plan, tv, xo, s, d_acc, d_counters, d_status);
+    }
+}

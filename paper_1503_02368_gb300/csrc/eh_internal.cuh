@@ -1,0 +1,170 @@
+// eh_internal.cuh -- shared definitions of the CUDA implementation of eh.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+#include <map>
+
+#include "../../include/eh.h"
+
+// ------------------------------------------------------------------ errors
+
+void eh_set_error(const char *fmt, ...);
+
+#define EH_CUDA_TRY(call)                                                                       \
+    do {                                                                                        \
+        cudaError_t _e = (call);                                                                \
+        if (_e != cudaSuccess) {                                                                \
+            eh_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(_e));     \
+            return _e == cudaErrorMemoryAllocation ? EH_ENOMEM : EH_ECUDA;                      \
+        }                                                                                       \
+    } while (0)
+
+#define EH_TRY(call)                                   \
+    do {                                               \
+        eh_status _s = (call);                         \
+        if (_s != EH_OK) return _s;                    \
+    } while (0)
+
+// device-side status bits (written with atomicOr, read by the host)
+enum : uint32_t {
+    DEV_ST_TIMEOUT = 1u,   // a bounded mbarrier wait gave up
+    DEV_ST_OVERFLOW = 2u,  // an accumulator passed 2^63
+    DEV_ST_INVALID = 4u,   // an input id was out of range
+};
+
+// ------------------------------------------------------------ set layouts
+//
+// Every pruned set N+(v) is kept as a sorted uint32 array in `nbr`, starting
+// on a 16-byte boundary and padded to a multiple of four elements with
+// EH_PAD (never a valid id).  When the set-level rule selects the bitset
+// layout, a bitset copy is kept as well: `nwords` 32-bit words starting at
+// word `woff` of the bitset pool, bit b of word i standing for the value
+// 32*(lo_word+i)+b.  lo_word and nwords are multiples of 4, so that two
+// bitsets line up on 128-bit vectors.
+#define EH_PAD 0xFFFFFFFFu
+
+struct __align__(16) SetDesc {
+    uint64_t off;      // element offset of the uint array in nbr (multiple of 4)
+    uint32_t len;      // |N+(v)|
+    uint32_t deg;      // d(v) in the symmetric graph
+    uint64_t woff;     // word offset of the bitset in words (multiple of 4)
+    uint32_t lo_word;  // first covered word, value/32 (multiple of 4)
+    uint32_t nwords;   // 0 = uint layout only
+};
+
+// The device view of one pruned trie (whole graph or one induced subgraph).
+struct TrieView {
+    const SetDesc *desc;    // per vertex
+    const uint32_t *nbr;    // uint arrays
+    const uint32_t *words;  // bitset pool
+    const uint32_t *deg;    // d(v), symmetric degree
+    uint32_t n;
+};
+
+// per-pattern work lists (vertex ids, heaviest first)
+struct WorkPlan {
+    uint32_t light_max = 0;
+    uint32_t *d_heavy = nullptr;   // |N+(u)| > light_max
+    uint32_t n_heavy = 0;
+    uint32_t *d_light = nullptr;   // 2 <= |N+(u)| <= light_max
+    uint32_t n_light = 0;
+    double alg_bytes = 0;          // algorithmic bytes of one triangle pass
+    double alg_bytes_k4 = 0;       // algorithmic bytes of one 4-clique pass
+};
+
+struct eh_trie {
+    uint32_t n = 0;         // id space
+    uint32_t n_active = 0;  // vertices with degree > 0 (new ids [0, n_active))
+    uint32_t nb = 1;        // bits for an id
+    uint64_t m = 0;         // unique undirected edges
+    uint32_t max_deg = 0, max_out = 0;
+    eh_build_opts opts{};
+
+    uint32_t *d_new2old = nullptr, *d_old2new = nullptr;
+    // symmetric trie N(v)
+    uint64_t *d_soff = nullptr;   // n+1 padded offsets
+    uint32_t *d_snbr = nullptr;
+    uint64_t snbr_len = 0;
+    // pruned trie N+(v)
+    SetDesc *d_desc = nullptr;    // n
+    uint32_t *d_onbr = nullptr;
+    uint64_t onbr_len = 0;
+    uint32_t *d_words = nullptr;
+    uint64_t n_words = 0;
+    uint32_t *d_deg = nullptr;    // n, symmetric degree (new ids)
+    uint64_t n_bitset = 0, n_nonempty = 0;
+    double density_skew = 0;
+    uint64_t device_bytes = 0;
+
+    // scratch owned by the trie: counters, accumulators, status
+    unsigned long long *d_scratch = nullptr;  // 16 words
+    uint32_t *d_arena = nullptr;              // 4-clique spill arena for large S sets
+    uint64_t arena_words = 0;
+    uint32_t *d_status = nullptr;
+
+    std::mutex mu;        // guards plans
+    std::mutex call_mu;   // serialises synchronous counts (they share d_scratch)
+    std::map<uint32_t, WorkPlan> plans;   // keyed by light_max
+
+    TrieView view() const {
+        TrieView v;
+        v.desc = d_desc; v.nbr = d_onbr; v.words = d_words; v.deg = d_deg; v.n = n;
+        return v;
+    }
+};
+
+// ------------------------------------------------------------- primitives
+
+// Exclusive prefix sum of n values (in may equal out).  Returns the total in
+// *total_host when non-null (synchronises the stream).
+eh_status dev_exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, cudaStream_t s,
+                                 uint64_t *total_host);
+eh_status dev_exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
+                                 uint64_t *total_host);
+// Stable LSD radix sort of keys on bits [0, key_bits); result in *keys
+// (the two buffers may be swapped on return).
+eh_status dev_radix_sort_u64(uint64_t **keys, uint64_t **tmp, uint64_t n, int key_bits, cudaStream_t s);
+
+// Device memory helpers (stream-ordered).
+template <typename T>
+eh_status dev_alloc(T **p, uint64_t count, cudaStream_t s) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void **)p, sizeof(T) * count, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        eh_set_error("device allocation of %llu bytes failed: %s", (unsigned long long)(sizeof(T) * count),
+                     cudaGetErrorString(e));
+        return EH_ENOMEM;
+    }
+    return EH_OK;
+}
+
+template <typename T>
+void dev_free(T *&p, cudaStream_t s) {
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+static inline uint32_t ceil_div_u32(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+int eh_num_sms();
+
+// Count entry points shared between files.
+eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan **out);
+eh_status eh_launch_triangle(const eh_trie *t, const WorkPlan &plan, TrieView tv, int mode,
+                             const eh_exec_opts &xo, cudaStream_t s, unsigned long long *d_acc,
+                             unsigned long long *d_counters, uint32_t *d_status, unsigned long long *d_vt,
+                             const uint32_t *d_qid);
+eh_status eh_launch_clique4(const eh_trie *t, const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo,
+                            cudaStream_t s, unsigned long long *d_acc, unsigned long long *d_counters,
+                            uint32_t *d_status, uint32_t *d_arena, uint64_t arena_words_per_warp);
+eh_exec_opts eh_exec_defaults(const eh_exec_opts *x);

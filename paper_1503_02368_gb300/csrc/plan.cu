@@ -1,0 +1,146 @@
+// plan.cu -- the per-vertex work list of the pruned trie (cost estimate,
+// light/heavy split by |N+(u)|, heaviest first) and the algorithmic byte
+// count of one triangle pass.
+#include "eh_internal.cuh"
+
+namespace {
+
+// one warp per vertex: cost(u) = sum_{v in N+(u)} |N+(v)|, and the bytes
+// the method must move for u: A = N+(u) once (its cheaper stored form), then
+// per pair (u, v = A[j]) the cheapest way to read what of B = N+(v) can meet
+// A_<v: the uint array (4|B| bytes; at most 32 bytes per probe of the j
+// elements of A_<v when |B| > ratio*j, the galloping side), or the bitset
+// words overlapping A's value range (at most 32 bytes per probe of A_<v).
+// A lower bound on what any of the kernel's dispatch choices reads.
+__global__ void k_cost(TrieView tv, uint32_t n, uint32_t ratio, uint64_t *cost, unsigned long long *bytes_acc) {
+    uint32_t u = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= n) return;
+    SetDesc du = tv.desc[u];
+    uint64_t c = 0, b = 0;
+    if (du.len >= 2) {
+        const uint32_t first = tv.nbr[du.off], last = tv.nbr[du.off + du.len - 1];
+        const uint32_t a_lo = (first >> 7) << 2, a_hi = (last >> 5) + 1;   // A's word range
+        for (uint32_t j = lane; j < du.len; j += 32) {
+            uint32_t v = tv.nbr[du.off + j];
+            SetDesc dv = tv.desc[v];
+            c += dv.len;
+            if (j == 0 || dv.len == 0) continue;
+            uint64_t bb = 4ull * dv.len;
+            if ((uint64_t)dv.len > (uint64_t)ratio * j && 32ull * j < bb) bb = 32ull * j;
+            if (dv.nwords) {
+                uint32_t lo = a_lo > dv.lo_word ? a_lo : dv.lo_word;
+                uint32_t hi = a_hi < dv.lo_word + dv.nwords ? a_hi : dv.lo_word + dv.nwords;
+                uint64_t wb = hi > lo ? 4ull * (hi - lo) : 0ull;
+                if (32ull * j < wb) wb = 32ull * j;
+                if (wb < bb) bb = wb;
+            }
+            b += bb;
+        }
+        if (lane == 0) b += du.nwords && du.nwords < du.len ? 4ull * du.nwords : 4ull * du.len;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, d);
+        b += __shfl_xor_sync(0xffffffffu, b, d);
+    }
+    if (lane == 0) {
+        cost[u] = c;
+        if (b) atomicAdd(bytes_acc, (unsigned long long)b);
+    }
+}
+
+// class 0: heavy (len > light_max), 1: light (2 <= len <= light_max)
+__global__ void k_class_flags(TrieView tv, uint32_t n, uint32_t light_max, int cls, uint32_t *flags) {
+    uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    uint32_t len = tv.desc[u].len;
+    bool f = cls == 0 ? len > light_max : (len >= 2 && len <= light_max);
+    flags[u] = f ? 1u : 0u;
+}
+
+__global__ void k_class_keys(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
+                             const uint64_t *__restrict__ cost, uint32_t n, int nb, int cbits, uint64_t *keys) {
+    uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n || !flags[u]) return;
+    uint64_t cmax = (1ull << cbits) - 1;
+    uint64_t c = cost[u] < cmax ? cost[u] : cmax;
+    keys[pos[u]] = ((cmax - c) << nb) | u;   // ascending key = descending cost
+}
+
+__global__ void k_key_ids(const uint64_t *__restrict__ keys, uint32_t cnt, int nb, uint32_t *ids) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) ids[i] = (uint32_t)(keys[i] & ((1ull << nb) - 1));
+}
+
+eh_status make_list(TrieView tv, uint32_t n, int nb, uint32_t light_max, int cls, const uint64_t *cost,
+                    cudaStream_t s, uint32_t **out, uint32_t *count) {
+    *out = nullptr;
+    *count = 0;
+    uint32_t *flags = nullptr, *pos = nullptr;
+    EH_TRY(dev_alloc(&flags, n, s));
+    eh_status st = dev_alloc(&pos, n, s);
+    if (st != EH_OK) { dev_free(flags, s); return st; }
+    unsigned blocks = (n + 255) / 256;
+    uint64_t cnt = 0;
+    if (n) k_class_flags<<<blocks, 256, 0, s>>>(tv, n, light_max, cls, flags);
+    st = dev_exclusive_scan_u32(flags, pos, n, s, &cnt);
+    uint64_t *k1 = nullptr, *k2 = nullptr;
+    if (st == EH_OK) st = dev_alloc(&k1, cnt, s);
+    if (st == EH_OK) st = dev_alloc(&k2, cnt, s);
+    int cbits = 64 - nb < 40 ? 64 - nb : 40;
+    if (st == EH_OK && cnt) {
+        k_class_keys<<<blocks, 256, 0, s>>>(flags, pos, cost, n, nb, cbits, k1);
+        st = dev_radix_sort_u64(&k1, &k2, cnt, nb + cbits, s);
+    }
+    uint32_t *ids = nullptr;
+    if (st == EH_OK) {
+        cudaError_t e = cudaMalloc((void **)&ids, (cnt ? cnt : 1) * 4);
+        if (e != cudaSuccess) { cudaGetLastError(); eh_set_error("work list allocation failed"); st = EH_ENOMEM; }
+    }
+    if (st == EH_OK && cnt) k_key_ids<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(k1, (uint32_t)cnt, nb, ids);
+    dev_free(k1, s);
+    dev_free(k2, s);
+    dev_free(flags, s);
+    dev_free(pos, s);
+    if (st != EH_OK) { cudaFree(ids); return st; }
+    *out = ids;
+    *count = (uint32_t)cnt;
+    return EH_OK;
+}
+
+}  // namespace
+
+eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan **out) {
+    std::lock_guard<std::mutex> g(t->mu);
+    auto it = t->plans.find(light_max);
+    if (it != t->plans.end()) { *out = &it->second; return EH_OK; }
+    WorkPlan p;
+    p.light_max = light_max;
+    TrieView tv = t->view();
+    uint64_t *cost = nullptr;
+    unsigned long long *bytes_d = nullptr;
+    EH_TRY(dev_alloc(&cost, t->n, s));
+    eh_status st = dev_alloc(&bytes_d, 1, s);
+    if (st == EH_OK) {
+        cudaMemsetAsync(bytes_d, 0, 8, s);
+        if (t->n) k_cost<<<(t->n + 7) / 8, 256, 0, s>>>(tv, t->n, 32, cost, bytes_d);
+        st = make_list(tv, t->n, t->nb, light_max, 0, cost, s, &p.d_heavy, &p.n_heavy);
+    }
+    if (st == EH_OK) st = make_list(tv, t->n, t->nb, light_max, 1, cost, s, &p.d_light, &p.n_light);
+    unsigned long long bytes_h = 0;
+    if (st == EH_OK) {
+        cudaMemcpyAsync(&bytes_h, bytes_d, 8, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { eh_set_error("plan: %s", cudaGetErrorString(cudaGetLastError())); st = EH_ECUDA; }
+    }
+    dev_free(cost, s);
+    dev_free(bytes_d, s);
+    if (st != EH_OK) {
+        cudaFree(p.d_heavy);
+        cudaFree(p.d_light);
+        return st;
+    }
+    p.alg_bytes = (double)bytes_h + 8.0 * (double)t->m;
+    auto res = t->plans.emplace(light_max, p);
+    *out = &res.first->second;
+    return EH_OK;
+}

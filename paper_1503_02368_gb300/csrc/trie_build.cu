@@ -1,0 +1,496 @@
+// trie_build.cu -- eh_build_trie: edge list -> device-resident two-level trie.
+//
+// Steps (EmptyHeaded Sec. 2.2 and 4.4, App. A.1):
+//   1. canonical undirected pairs (lo, hi), self-loops dropped, ids checked;
+//   2. radix sort + unique: the simple edge relation (m edges);
+//   3. degrees, then new ids by (degree desc, original id asc) -- the
+//      "Degree" node ordering;
+//   4. both index orders of every edge in new ids, radix sorted: the
+//      symmetric trie N(v); its prefix of smaller ids is the pruned trie N+(v)
+//      (each undirected edge kept in the set of its larger endpoint);
+//   5. per-set layout: a bitset copy of N+(v) when range <= tau*|N+(v)|.
+#include "eh_internal.cuh"
+
+#include <cmath>
+#include <new>
+#include <algorithm>
+
+namespace {
+
+__global__ void k_canon_keys(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst, uint64_t ne,
+                             uint32_t n, int nb, uint64_t *keys, uint32_t *status) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    uint32_t a = src[i], b = dst[i];
+    if (a >= n || b >= n) {
+        atomicOr(status, DEV_ST_INVALID);
+        keys[i] = ~0ull;
+        return;
+    }
+    if (a == b) { keys[i] = ~0ull; return; }
+    uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+    keys[i] = ((uint64_t)lo << nb) | hi;
+}
+
+__global__ void k_unique_flags(const uint64_t *__restrict__ keys, uint64_t ne, uint32_t *flags) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    uint64_t k = keys[i];
+    flags[i] = (k != ~0ull && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+}
+
+__global__ void k_unique_scatter(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ flags,
+                                 const uint32_t *__restrict__ pos, uint64_t ne, uint64_t *out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    if (flags[i]) out[pos[i]] = keys[i];
+}
+
+__global__ void k_degrees(const uint64_t *__restrict__ ukeys, uint64_t m, int nb, uint32_t *deg) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint64_t k = ukeys[i];
+    uint32_t lo = (uint32_t)(k >> nb), hi = (uint32_t)(k & ((1ull << nb) - 1));
+    atomicAdd(&deg[lo], 1u);
+    atomicAdd(&deg[hi], 1u);
+}
+
+__global__ void k_max_u32(const uint32_t *__restrict__ x, uint64_t n, uint32_t *out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t v = i < n ? x[i] : 0u;
+    for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, d));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
+}
+
+__global__ void k_order_keys(const uint32_t *__restrict__ deg, uint32_t n, uint32_t maxdeg, int nb,
+                             uint64_t *keys) {
+    uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    keys[v] = ((uint64_t)(maxdeg - deg[v]) << nb) | v;
+}
+
+__global__ void k_relabel_maps(const uint64_t *__restrict__ keys, uint32_t n, int nb, const uint32_t *__restrict__ deg_old,
+                               uint32_t *new2old, uint32_t *old2new, uint32_t *deg_new) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t old = (uint32_t)(keys[i] & ((1ull << nb) - 1));
+    new2old[i] = old;
+    old2new[old] = (uint32_t)i;
+    deg_new[i] = deg_old[old];
+}
+
+__global__ void k_directed_keys(const uint64_t *__restrict__ ukeys, uint64_t m, int nb,
+                                const uint32_t *__restrict__ old2new, uint64_t *dk) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint64_t k = ukeys[i];
+    uint32_t a = old2new[(uint32_t)(k >> nb)], b = old2new[(uint32_t)(k & ((1ull << nb) - 1))];
+    dk[2 * i] = ((uint64_t)a << nb) | b;
+    dk[2 * i + 1] = ((uint64_t)b << nb) | a;
+}
+
+__global__ void k_round4(const uint32_t *__restrict__ x, uint64_t n, uint64_t *out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ((uint64_t)x[i] + 3) & ~3ull;
+}
+
+__global__ void k_widen(const uint32_t *__restrict__ x, uint64_t n, uint64_t *out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = x[i];
+}
+
+// place sorted directed edge i = (v, w) at soff[v] + (i - ustart[v])
+__global__ void k_fill_sym(const uint64_t *__restrict__ dk, uint64_t n2, int nb, const uint64_t *__restrict__ ustart,
+                           const uint64_t *__restrict__ soff, uint32_t *snbr, uint32_t *odeg) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    uint64_t k = dk[i];
+    uint32_t v = (uint32_t)(k >> nb), w = (uint32_t)(k & ((1ull << nb) - 1));
+    snbr[soff[v] + (i - ustart[v])] = w;
+    if (w < v) atomicAdd(&odeg[v], 1u);
+}
+
+// N+(v) is the prefix of N(v) below v
+__global__ void k_fill_pruned(const uint32_t *__restrict__ snbr, const uint64_t *__restrict__ soff,
+                              const uint64_t *__restrict__ ooff, const uint32_t *__restrict__ odeg, uint32_t n,
+                              uint32_t *onbr) {
+    uint32_t v = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (v >= n) return;
+    uint32_t len = odeg[v];
+    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) onbr[ooff[v] + j] = snbr[soff[v] + j];
+}
+
+// set-level layout rule (Sec. 4.4): words needed by each set's bitset, 0 = uint
+__global__ void k_layout(const uint32_t *__restrict__ onbr, const uint64_t *__restrict__ ooff,
+                         const uint32_t *__restrict__ odeg, uint32_t n, uint32_t tau, uint32_t min_len,
+                         uint64_t *nwords, uint32_t *lo_word) {
+    uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    uint32_t len = odeg[v];
+    uint64_t w = 0;
+    uint32_t lw = 0;
+    if (len > 0 && tau > 0 && len >= min_len) {
+        uint32_t first = onbr[ooff[v]], last = onbr[ooff[v] + len - 1];
+        uint64_t range = (uint64_t)last - first + 1;
+        if (tau == 0xFFFFFFFFu || range <= (uint64_t)tau * len) {
+            lw = (first >> 7) << 2;                       // 128-bit aligned
+            uint64_t hw = (last >> 5) + 1;
+            w = (hw - lw + 3) & ~3ull;
+        }
+    }
+    nwords[v] = w;
+    lo_word[v] = lw;
+}
+
+__global__ void k_fill_bits(const uint32_t *__restrict__ onbr, const uint64_t *__restrict__ ooff,
+                            const uint32_t *__restrict__ odeg, const uint64_t *__restrict__ nwords,
+                            const uint64_t *__restrict__ woff, const uint32_t *__restrict__ lo_word, uint32_t n,
+                            uint32_t *words) {
+    uint32_t v = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (v >= n || nwords[v] == 0) return;
+    uint32_t len = odeg[v];
+    uint64_t base = woff[v];
+    uint32_t lw = lo_word[v];
+    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+        uint32_t x = onbr[ooff[v] + j];
+        atomicOr(&words[base + ((x >> 5) - lw)], 1u << (x & 31));
+    }
+}
+
+__global__ void k_desc(const uint64_t *__restrict__ ooff, const uint32_t *__restrict__ odeg,
+                       const uint32_t *__restrict__ sdeg, const uint64_t *__restrict__ nwords,
+                       const uint64_t *__restrict__ woff, const uint32_t *__restrict__ lo_word, uint32_t n,
+                       SetDesc *desc) {
+    uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    SetDesc d;
+    d.off = ooff[v];
+    d.len = odeg[v];
+    d.deg = sdeg[v];
+    d.woff = nwords[v] ? woff[v] : 0;
+    d.lo_word = lo_word[v];
+    d.nwords = (uint32_t)nwords[v];
+    desc[v] = d;
+}
+
+inline unsigned blocks_for(uint64_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
+
+int bits_for(uint64_t n) {   // bits to represent values in [0, n)
+    int b = 1;
+    while (b < 63 && (1ull << b) < n) ++b;
+    return b;
+}
+
+void free_trie_arrays(eh_trie *t) {
+    cudaFree(t->d_new2old); cudaFree(t->d_old2new); cudaFree(t->d_soff); cudaFree(t->d_snbr);
+    cudaFree(t->d_desc); cudaFree(t->d_onbr); cudaFree(t->d_words); cudaFree(t->d_deg);
+    cudaFree(t->d_scratch); cudaFree(t->d_status); cudaFree(t->d_arena);
+    for (auto &kv : t->plans) { cudaFree(kv.second.d_heavy); cudaFree(kv.second.d_light); }
+    t->plans.clear();
+}
+
+template <typename T>
+eh_status persist_alloc(T **p, uint64_t count, uint64_t *bytes) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        eh_set_error("device allocation of %llu bytes failed: %s", (unsigned long long)(sizeof(T) * count),
+                     cudaGetErrorString(e));
+        return EH_ENOMEM;
+    }
+    *bytes += sizeof(T) * count;
+    return EH_OK;
+}
+
+// Scope guard for stream-ordered temporaries.
+struct Temps {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Temps(cudaStream_t st) : s(st) {}
+    template <typename T>
+    eh_status alloc(T **p, uint64_t count) {
+        eh_status st = dev_alloc(p, count, s);
+        if (st == EH_OK) ptrs.push_back((void *)*p);
+        return st;
+    }
+    template <typename T>
+    void release(T *&p) {
+        for (auto &q : ptrs)
+            if (q == (void *)p) { cudaFreeAsync(q, s); q = nullptr; }
+        p = nullptr;
+    }
+    ~Temps() {
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, s);
+    }
+};
+
+eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t n, const eh_build_opts &o,
+                cudaStream_t s, eh_trie *t) {
+    Temps tmp(s);
+    uint64_t bytes = 0;
+    const int nb = bits_for(n);
+    t->nb = nb;
+    if (2 * nb > 64) { eh_set_error("id space too large"); return EH_EINVAL; }
+
+    // scratch shared by the count kernels
+    EH_TRY(persist_alloc(&t->d_scratch, 16, &bytes));
+    EH_TRY(persist_alloc(&t->d_status, 4, &bytes));
+    EH_CUDA_TRY(cudaMemsetAsync(t->d_scratch, 0, 16 * sizeof(unsigned long long), s));
+    EH_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, 4 * sizeof(uint32_t), s));
+
+    // 0. inputs on the device
+    const uint32_t *d_src = src, *d_dst = dst;
+    if (!(o.flags & EH_BUILD_DEVICE_INPUT) && ne > 0) {
+        uint32_t *a = nullptr, *b = nullptr;
+        EH_TRY(tmp.alloc(&a, ne));
+        EH_TRY(tmp.alloc(&b, ne));
+        EH_CUDA_TRY(cudaMemcpyAsync(a, src, ne * 4, cudaMemcpyHostToDevice, s));
+        EH_CUDA_TRY(cudaMemcpyAsync(b, dst, ne * 4, cudaMemcpyHostToDevice, s));
+        d_src = a;
+        d_dst = b;
+    }
+
+    // 1-2. canonical keys, sort, unique
+    uint64_t *keys = nullptr, *keys2 = nullptr, *ukeys = nullptr;
+    uint32_t *flags = nullptr, *pos = nullptr;
+    uint64_t m = 0;
+    if (ne > 0) {
+        EH_TRY(tmp.alloc(&keys, ne));
+        EH_TRY(tmp.alloc(&keys2, ne));
+        k_canon_keys<<<blocks_for(ne), 256, 0, s>>>(d_src, d_dst, ne, n, nb, keys, t->d_status);
+        uint32_t st_h = 0;
+        EH_CUDA_TRY(cudaMemcpyAsync(&st_h, t->d_status, 4, cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaStreamSynchronize(s));
+        if (st_h & DEV_ST_INVALID) {
+            eh_set_error("an edge endpoint is >= n_vertices (%u)", n);
+            return EH_EINVAL;
+        }
+        EH_TRY(dev_radix_sort_u64(&keys, &keys2, ne, 2 * nb, s));
+        EH_TRY(tmp.alloc(&flags, ne));
+        EH_TRY(tmp.alloc(&pos, ne));
+        k_unique_flags<<<blocks_for(ne), 256, 0, s>>>(keys, ne, flags);
+        EH_TRY(dev_exclusive_scan_u32(flags, pos, ne, s, &m));
+        EH_TRY(tmp.alloc(&ukeys, m));
+        k_unique_scatter<<<blocks_for(ne), 256, 0, s>>>(keys, flags, pos, ne, ukeys);
+        tmp.release(flags);
+        tmp.release(pos);
+        tmp.release(keys);
+        tmp.release(keys2);
+    }
+    t->m = m;
+
+    // 3. degrees and the degree ordering
+    uint32_t *deg_old = nullptr, *d_max = nullptr;
+    EH_TRY(tmp.alloc(&deg_old, n));
+    EH_TRY(tmp.alloc(&d_max, 1));
+    EH_CUDA_TRY(cudaMemsetAsync(deg_old, 0, (uint64_t)n * 4, s));
+    EH_CUDA_TRY(cudaMemsetAsync(d_max, 0, 4, s));
+    if (m) k_degrees<<<blocks_for(m), 256, 0, s>>>(ukeys, m, nb, deg_old);
+    if (n) k_max_u32<<<blocks_for(n), 256, 0, s>>>(deg_old, n, d_max);
+    uint32_t maxdeg = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&maxdeg, d_max, 4, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    t->max_deg = maxdeg;
+
+    EH_TRY(persist_alloc(&t->d_new2old, n, &bytes));
+    EH_TRY(persist_alloc(&t->d_old2new, n, &bytes));
+    EH_TRY(persist_alloc(&t->d_deg, n, &bytes));
+    {
+        uint64_t *ok = nullptr, *ok2 = nullptr;
+        EH_TRY(tmp.alloc(&ok, n));
+        EH_TRY(tmp.alloc(&ok2, n));
+        if (n) k_order_keys<<<blocks_for(n), 256, 0, s>>>(deg_old, n, maxdeg, nb, ok);
+        EH_TRY(dev_radix_sort_u64(&ok, &ok2, n, nb + bits_for((uint64_t)maxdeg + 1), s));
+        if (n) k_relabel_maps<<<blocks_for(n), 256, 0, s>>>(ok, n, nb, deg_old, t->d_new2old, t->d_old2new, t->d_deg);
+        tmp.release(ok);
+        tmp.release(ok2);
+    }
+
+    // 4. both index orders in new ids; symmetric and pruned tries
+    const uint64_t n2 = 2 * m;
+    uint64_t *dk = nullptr, *dk2 = nullptr;
+    EH_TRY(tmp.alloc(&dk, n2));
+    EH_TRY(tmp.alloc(&dk2, n2));
+    if (m) k_directed_keys<<<blocks_for(m), 256, 0, s>>>(ukeys, m, nb, t->d_old2new, dk);
+    tmp.release(ukeys);
+    EH_TRY(dev_radix_sort_u64(&dk, &dk2, n2, 2 * nb, s));
+    tmp.release(dk2);
+
+    uint64_t *ustart = nullptr, *wide = nullptr;
+    EH_TRY(tmp.alloc(&ustart, (uint64_t)n + 1));
+    EH_TRY(tmp.alloc(&wide, (uint64_t)n + 1));
+    EH_TRY(persist_alloc(&t->d_soff, (uint64_t)n + 1, &bytes));
+    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
+    if (n) k_widen<<<blocks_for(n), 256, 0, s>>>(t->d_deg, n, wide);
+    EH_TRY(dev_exclusive_scan_u64(wide, ustart, (uint64_t)n + 1, s, nullptr));
+    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
+    if (n) k_round4<<<blocks_for(n), 256, 0, s>>>(t->d_deg, n, wide);
+    uint64_t slen = 0;
+    EH_TRY(dev_exclusive_scan_u64(wide, t->d_soff, (uint64_t)n + 1, s, &slen));
+    t->snbr_len = slen;
+    EH_TRY(persist_alloc(&t->d_snbr, slen, &bytes));
+    EH_CUDA_TRY(cudaMemsetAsync(t->d_snbr, 0xFF, (slen ? slen : 1) * 4, s));
+    uint32_t *odeg = nullptr;
+    EH_TRY(tmp.alloc(&odeg, n));
+    EH_CUDA_TRY(cudaMemsetAsync(odeg, 0, (uint64_t)n * 4, s));
+    if (n2) k_fill_sym<<<blocks_for(n2), 256, 0, s>>>(dk, n2, nb, ustart, t->d_soff, t->d_snbr, odeg);
+    tmp.release(dk);
+
+    uint64_t *ooff = nullptr;
+    EH_TRY(tmp.alloc(&ooff, (uint64_t)n + 1));
+    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
+    if (n) k_round4<<<blocks_for(n), 256, 0, s>>>(odeg, n, wide);
+    uint64_t olen = 0;
+    EH_TRY(dev_exclusive_scan_u64(wide, ooff, (uint64_t)n + 1, s, &olen));
+    t->onbr_len = olen;
+    EH_TRY(persist_alloc(&t->d_onbr, olen, &bytes));
+    EH_CUDA_TRY(cudaMemsetAsync(t->d_onbr, 0xFF, (olen ? olen : 1) * 4, s));
+    if (n) k_fill_pruned<<<blocks_for(n, 8), 256, 0, s>>>(t->d_snbr, t->d_soff, ooff, odeg, n, t->d_onbr);
+
+    // 5. layouts
+    uint64_t *nwords = nullptr, *woff = nullptr;
+    uint32_t *lo_word = nullptr;
+    EH_TRY(tmp.alloc(&nwords, (uint64_t)n + 1));
+    EH_TRY(tmp.alloc(&woff, (uint64_t)n + 1));
+    EH_TRY(tmp.alloc(&lo_word, (uint64_t)n + 1));
+    EH_CUDA_TRY(cudaMemsetAsync(nwords, 0, ((uint64_t)n + 1) * 8, s));
+    if (n) k_layout<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, ooff, odeg, n, o.bitset_tau, o.min_bitset_len, nwords, lo_word);
+    uint64_t tw = 0;
+    EH_TRY(dev_exclusive_scan_u64(nwords, woff, (uint64_t)n + 1, s, &tw));
+    t->n_words = tw;
+    EH_TRY(persist_alloc(&t->d_words, tw, &bytes));
+    EH_CUDA_TRY(cudaMemsetAsync(t->d_words, 0, (tw ? tw : 1) * 4, s));
+    if (n) k_fill_bits<<<blocks_for(n, 8), 256, 0, s>>>(t->d_onbr, ooff, odeg, nwords, woff, lo_word, n, t->d_words);
+    EH_TRY(persist_alloc(&t->d_desc, n, &bytes));
+    if (n) k_desc<<<blocks_for(n), 256, 0, s>>>(ooff, odeg, t->d_deg, nwords, woff, lo_word, n, t->d_desc);
+
+    // stats (host side, diagnostics only)
+    std::vector<uint32_t> hdeg(n), hodeg(n);
+    std::vector<uint64_t> hnw(n);
+    if (n) {
+        EH_CUDA_TRY(cudaMemcpyAsync(hdeg.data(), t->d_deg, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaMemcpyAsync(hodeg.data(), odeg, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaMemcpyAsync(hnw.data(), nwords, (uint64_t)n * 8, cudaMemcpyDeviceToHost, s));
+    }
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    EH_CUDA_TRY(cudaGetLastError());
+    uint32_t act = 0, mo = 0;
+    uint64_t nbs = 0, nne = 0;
+    double sum = 0, sum2 = 0;
+    std::map<uint32_t, uint64_t> hist;
+    for (uint32_t v = 0; v < n; ++v) {
+        if (hdeg[v]) ++act;
+        mo = std::max(mo, hodeg[v]);
+        if (hodeg[v]) ++nne;
+        if (hnw[v]) ++nbs;
+        sum += hdeg[v];
+        sum2 += (double)hdeg[v] * hdeg[v];
+        hist[hdeg[v]]++;
+    }
+    t->n_active = act;
+    t->max_out = mo;
+    t->n_bitset = nbs;
+    t->n_nonempty = nne;
+    double mean = n ? sum / n : 0, var = n ? sum2 / n - mean * mean : 0;
+    uint32_t mode = 0;
+    uint64_t best = 0;
+    for (auto &kv : hist)
+        if (kv.second > best) { best = kv.second; mode = kv.first; }
+    t->density_skew = var > 0 ? 3.0 * (mean - mode) / std::sqrt(var) : 0.0;
+    t->device_bytes = bytes;
+    return EH_OK;
+}
+
+}  // namespace
+
+extern "C" eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uint64_t n_edges, uint32_t n_vertices,
+                                   const eh_build_opts *opts, void *stream, eh_trie **out) {
+    if (!out) { eh_set_error("eh_build_trie: out is NULL"); return EH_EINVAL; }
+    *out = nullptr;
+    if (n_edges > 0 && (!src || !dst)) { eh_set_error("eh_build_trie: src/dst NULL"); return EH_EINVAL; }
+    if (n_vertices > 0xFFE00000u) { eh_set_error("eh_build_trie: n_vertices above 0xFFE00000"); return EH_EINVAL; }
+    if (n_edges >= (1ull << 31)) { eh_set_error("eh_build_trie: more than 2^31 input edges"); return EH_EINVAL; }
+    eh_build_opts o;
+    o.bitset_tau = 32;
+    o.min_bitset_len = 0;
+    o.flags = 0;
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    eh_trie *t = new (std::nothrow) eh_trie();
+    if (!t) { eh_set_error("host allocation failed"); return EH_ENOMEM; }
+    t->n = n_vertices;
+    t->opts = o;
+    eh_status st = build(src, dst, n_edges, n_vertices, o, s, t);
+    if (st != EH_OK) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        free_trie_arrays(t);
+        delete t;
+        return st;
+    }
+    *out = t;
+    return EH_OK;
+}
+
+extern "C" void eh_free_trie(eh_trie *t) {
+    if (!t) return;
+    cudaDeviceSynchronize();
+    free_trie_arrays(t);
+    delete t;
+}
+
+extern "C" eh_status eh_trie_stats_get(const eh_trie *t, eh_trie_stats *o) {
+    if (!t || !o) { eh_set_error("eh_trie_stats_get: NULL argument"); return EH_EINVAL; }
+    memset(o, 0, sizeof(*o));
+    o->n_vertices = t->n;
+    o->n_active = t->n_active;
+    o->n_edges = t->m;
+    o->max_degree = t->max_deg;
+    o->max_out_degree = t->max_out;
+    o->n_bitset_sets = t->n_bitset;
+    o->n_nonempty_sets = t->n_nonempty;
+    o->bitset_words = t->n_words;
+    o->density_skew = t->density_skew;
+    o->device_bytes = t->device_bytes;
+    o->bitset_tau = t->opts.bitset_tau;
+    return EH_OK;
+}
+
+extern "C" eh_status eh_trie_export(const eh_trie *t, uint32_t which, uint32_t *new_to_old, uint64_t *out_off,
+                                    uint32_t *out_len, uint32_t *out_nbr, uint32_t *bits_lo, uint32_t *bits_nwords,
+                                    uint64_t *bits_off, uint32_t *out_words) {
+    if (!t || which > 1) { eh_set_error("eh_trie_export: bad argument"); return EH_EINVAL; }
+    const uint32_t n = t->n;
+    if (new_to_old && n) EH_CUDA_TRY(cudaMemcpy(new_to_old, t->d_new2old, (uint64_t)n * 4, cudaMemcpyDeviceToHost));
+    std::vector<SetDesc> desc(n);
+    if (n) EH_CUDA_TRY(cudaMemcpy(desc.data(), t->d_desc, (uint64_t)n * sizeof(SetDesc), cudaMemcpyDeviceToHost));
+    if (which == 0) {
+        for (uint32_t v = 0; v < n; ++v) {
+            if (out_off) out_off[v] = desc[v].off;
+            if (out_len) out_len[v] = desc[v].len;
+            if (bits_lo) bits_lo[v] = desc[v].nwords ? desc[v].lo_word * 32u : 0xFFFFFFFFu;
+            if (bits_nwords) bits_nwords[v] = desc[v].nwords;
+            if (bits_off) bits_off[v] = desc[v].woff;
+        }
+        if (out_off) out_off[n] = t->onbr_len;
+        if (out_nbr && t->onbr_len)
+            EH_CUDA_TRY(cudaMemcpy(out_nbr, t->d_onbr, t->onbr_len * 4, cudaMemcpyDeviceToHost));
+        if (out_words && t->n_words)
+            EH_CUDA_TRY(cudaMemcpy(out_words, t->d_words, t->n_words * 4, cudaMemcpyDeviceToHost));
+    } else {
+        if (out_off) EH_CUDA_TRY(cudaMemcpy(out_off, t->d_soff, ((uint64_t)n + 1) * 8, cudaMemcpyDeviceToHost));
+        if (out_len) for (uint32_t v = 0; v < n; ++v) out_len[v] = desc[v].deg;
+        if (out_nbr && t->snbr_len)
+            EH_CUDA_TRY(cudaMemcpy(out_nbr, t->d_snbr, t->snbr_len * 4, cudaMemcpyDeviceToHost));
+        for (uint32_t v = 0; v < n; ++v) {
+            if (bits_lo) bits_lo[v] = 0xFFFFFFFFu;
+            if (bits_nwords) bits_nwords[v] = 0;
+            if (bits_off) bits_off[v] = 0;
+        }
+    }
+    return EH_OK;
+}

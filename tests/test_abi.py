@@ -1,0 +1,60 @@
+"""The C-ABI library loads and exports every function include/eh.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1503_02368_gb300 as eh
+from paper_1503_02368_gb300 import eh as ehmod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(eh_\w+)\s*\(", src, flags=re.M):
+                names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = eh.lib()
+    names = declared_functions()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(ehmod.EXPORTED) <= names
+
+
+def test_last_error_is_callable_without_gpu():
+    L = eh.lib()
+    assert isinstance(L.eh_last_error(), bytes)
+
+
+def test_null_arguments_rejected_without_device_work():
+    L = eh.lib()
+    out = ctypes.c_uint64(0)
+    assert L.eh_count(None, 0, None, 0, None, ctypes.byref(out)) == 1
+    assert L.eh_count_async(None, 0, None, None, None) == 1
+    assert L.eh_build_trie(None, None, 0, 0, None, None, None) == 1
+    assert L.eh_trie_stats_get(None, None) == 1
+
+
+def test_structs_match_header_sizes():
+    assert ctypes.sizeof(ehmod.BuildOpts) == 12
+    assert ctypes.sizeof(ehmod.ExecOpts) == 16
+    assert ctypes.sizeof(ehmod.Query) == 16
+    assert ctypes.sizeof(ehmod.TrieStats) == 72
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    monkeypatch.setattr(ehmod, "_lib", None)
+    monkeypatch.setattr(ehmod, "_LIB_PATH", "/nonexistent/libeh.so")
+    with pytest.raises(RuntimeError):
+        ehmod.lib()

@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Counts are exact integers, so every comparison is bit-exact.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import workloads as W
+from tests import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "workload_counts.json")))
+PATS = ("triangle", "clique4", "lollipop", "lollipop_distinct")
+TAUS = (0, 1, 8, 32, 256, 0xFFFFFFFF)
+
+
+@pytest.fixture(scope="module")
+def eh():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1503_02368_gb300 as m
+    return m
+
+
+def both(eh, n, edges, tau=32):
+    s, d = G.arrays(edges)
+    return eh.Trie(s, d, n, tau=tau), oracle.Graph(n, s, d)
+
+
+# ------------------------------------------------------------------ trie build
+
+@pytest.mark.parametrize("seed", range(4))
+def test_trie_build_matches_oracle(eh, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(20, 400))
+    e = G.random_graph(n, float(rng.choice([0.02, 0.1, 0.4])), rng)
+    tau = [0, 8, 32, 0xFFFFFFFF][seed]
+    t, o = both(eh, n, e, tau)
+    x = t.export(0)
+    sym = t.export(1)
+    new2old = x["new_to_old"]
+    assert new2old.tolist() == o.degree_order().tolist()       # (degree desc, id asc)
+    old2new = np.empty(n, np.int64)
+    old2new[new2old] = np.arange(n)
+    st = t.stats()
+    assert st["n_edges"] == o.m
+    for v in range(n):
+        N = np.sort(old2new[o.neighbours(int(new2old[v]))]).astype(np.uint32)
+        b, ln = int(sym["off"][v]), int(sym["len"][v])
+        assert b % 4 == 0
+        assert np.array_equal(sym["nbr"][b:b + ln], N)
+        assert np.all(sym["nbr"][b + ln:int(sym["off"][v + 1])] == 0xFFFFFFFF)
+        P = N[N < v]
+        b, ln = int(x["off"][v]), int(x["len"][v])
+        assert b % 4 == 0 and ln == len(P)
+        assert np.array_equal(x["nbr"][b:b + ln], P)
+        # layout rule and bitset contents
+        is_bs = x["bits_nwords"][v] > 0
+        assert is_bs == oracle.layout_is_bitset(P, tau)
+        if is_bs:
+            lo, nw, wo = int(x["bits_lo"][v]), int(x["bits_nwords"][v]), int(x["bits_off"][v])
+            assert lo % 128 == 0 and nw % 4 == 0 and wo % 4 == 0
+            bits = np.unpackbits(x["words"][wo:wo + nw].view(np.uint8), bitorder="little")
+            assert np.array_equal(np.nonzero(bits)[0] + lo, P)
+
+
+def test_invalid_ids_rejected(eh):
+    with pytest.raises(eh.EHError) as ei:
+        eh.Trie(np.array([0, 5], np.uint32), np.array([1, 2], np.uint32), 5)
+    assert ei.value.status == 1
+
+
+def test_empty_graphs(eh):
+    t = eh.Trie(np.zeros(0, np.uint32), np.zeros(0, np.uint32), 10)
+    for p in PATS:
+        assert t.count(p) == 0
+    t0 = eh.Trie(np.zeros(0, np.uint32), np.zeros(0, np.uint32), 0)
+    assert t0.count("triangle") == 0
+    t1 = eh.Trie(np.array([3, 3], np.uint32), np.array([3, 3], np.uint32), 4)   # loops only
+    assert t1.count("triangle") == 0 and t1.stats()["n_edges"] == 0
+
+
+# ------------------------------------------------------------------ counts
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_graphs_all_patterns(eh, seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(10, 300))
+    e = G.random_graph(n, float(rng.choice([0.05, 0.2, 0.5, 0.8])), rng)
+    tau = TAUS[seed % len(TAUS)]
+    t, o = both(eh, n, e, tau)
+    for p in PATS:
+        assert t.count(p) == o.count(p), (p, tau)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 17, 33, 40, 64])
+def test_complete_graphs(eh, n):
+    t, _ = both(eh, n, G.complete(n))
+    assert t.count("triangle") == math.comb(n, 3)
+    assert t.count("clique4") == math.comb(n, 4)
+    assert t.count("lollipop") == n * (n - 1) * (n - 2) * (n - 1)
+
+
+def test_special_graphs(eh):
+    for n, e, tri, k4 in [(10, G.petersen(), 0, 0), (9, G.wheel(8), 8, 0)]:
+        t, _ = both(eh, n, e)
+        assert t.count("triangle") == tri and t.count("clique4") == k4
+    n, e = G.complete_multipartite(2, 2, 2, 2)
+    t, _ = both(eh, n, e)
+    assert t.count("clique4") == 16 and t.count("triangle") == 32
+
+
+@pytest.mark.parametrize("tau", TAUS)
+def test_layout_independence_rmat(eh, tau):
+    # Sec. 4.4: layouts change speed only; every tau gives the oracle's counts
+    g = W.rmat_graph(13, 1503 + 13)
+    o = oracle.Graph(g["n"], g["src"], g["dst"])
+    t = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+    for p in PATS:
+        assert t.count(p) == o.count(p, nthreads=8), (p, tau)
+
+
+@pytest.mark.parametrize("xo", [dict(gallop_ratio=1), dict(gallop_ratio=1000), dict(light_max=2),
+                                dict(light_max=8, cta_warps=4), dict(cta_warps=16), dict(light_max=32)])
+def test_exec_knobs_do_not_change_counts(eh, xo):
+    g = W.rmat_graph(12, 1503 + 12)
+    o = oracle.Graph(g["n"], g["src"], g["dst"])
+    for tau in (0, 32):
+        t = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+        x = eh.exec_opts(**xo)
+        for p in PATS:
+            assert t.count(p, xopts=x) == o.count(p, nthreads=8), (p, tau, xo)
+
+
+def test_hub_graph_spans_many_tiles(eh):
+    # a few hubs joined to everything: long sets (many 128-element chunks, ragged tails),
+    # on-chip bitmaps and sorted arrays for the large-range sets
+    rng = np.random.default_rng(7)
+    n = 70000
+    hubs = np.arange(6, dtype=np.uint32)
+    e = [(int(h), int(v)) for h in hubs for v in rng.choice(np.arange(6, n), 3000, replace=False)]
+    e += [(int(a), int(b)) for a, b in rng.integers(0, n, size=(40000, 2))]
+    e += [(0, 1), (1, 2), (0, 2), (2, 3), (3, 4)]
+    s, d = G.arrays(e)
+    o = oracle.Graph(n, s, d)
+    for tau in (0, 32, 0xFFFFFFFF):
+        t = eh.Trie(s, d, n, tau=tau)
+        for p in PATS:
+            assert t.count(p) == o.count(p, nthreads=8), (p, tau)
+
+
+def test_vertex_triangles_small(eh):
+    rng = np.random.default_rng(3)
+    n = 500
+    e = G.random_graph(n, 0.05, rng)
+    t, o = both(eh, n, e)
+    vt = t.vertex_triangles()
+    assert np.array_equal(vt, o.vertex_triangles(np.arange(n, dtype=np.uint32)))
+    assert int(vt.sum()) == 3 * o.triangles()
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_er_workload(eh):
+    g = W.er_10k_100k()
+    gold = GOLD["er_n10000_m100000"]
+    t = eh.Trie(g["src"], g["dst"], g["n"])
+    assert t.stats()["n_edges"] == gold["m"]
+    for p in PATS:
+        assert t.count(p) == gold[p], p
+
+
+def test_rmat16_workload(eh):
+    g = W.rmat_graph(16, 1503 + 16)
+    gold = GOLD["rmat_s16_ef16"]
+    from tests.golden.make_golden import fingerprint
+    assert fingerprint(g) == gold["fingerprint"]
+    for tau in (8, 32, 256):
+        t = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+        for p in PATS:
+            assert t.count(p) == gold[p], (p, tau)
+
+
+def test_rmat22_full_size(eh):
+    g = W.rmat22()
+    gold = GOLD["rmat_s22_ef16"]
+    from tests.golden.make_golden import fingerprint
+    assert fingerprint(g) == gold["fingerprint"]
+    t = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    assert t.stats()["n_edges"] == gold["m"]
+    assert t.count("triangle") == gold["triangle"]
+    vt = t.vertex_triangles()
+    for v, want in gold["vertex_triangles"].items():
+        assert int(vt[int(v)]) == want, v
+    assert int(vt.sum()) == 3 * gold["triangle"]
+    # lollipop by the same per-vertex counts (sum_x 2 t(x) d(x)) and degrees from the trie
+    sym = t.export(1)
+    deg = np.zeros(g["n"], np.uint64)
+    deg[sym["new_to_old"]] = sym["len"]
+    assert t.count("lollipop") == int((2 * vt.astype(object) * deg.astype(object)).sum())
+
+
+def test_chunglu_full_size(eh):
+    g = W.chunglu_1m()
+    gold = GOLD["chunglu_n1000000_g2.1"]
+    from tests.golden.make_golden import fingerprint
+    assert fingerprint(g) == gold["fingerprint"]
+    t = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    assert t.stats()["n_edges"] == gold["m"]
+    assert t.count("triangle") == gold["triangle"]
+    assert t.count("clique4") == gold["clique4"]

@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: exact triangle COUNT(*) on the R-MAT scale-22 graph (edges/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl eh|reference]
+
+One step = one whole-graph triangle count (eh_count_async) on the resident
+trie: the layout-dispatched intersection kernel over every (u, v) pair of
+the degree-pruned trie, plus its finalize kernel.  The trie build (index
+creation) is outside the step, as in the paper's timing rule (Sec. 5.1.3);
+the end-to-end figure (`e2e`) includes it, with the host edge list copied in
+and the count copied out inside the timed region.
+
+N > 1 (torchrun): every rank counts its own replica of the graph
+(independent problems, no collective on the data path); the value is the
+edges of all replicas over the slowest rank's time.
+
+The reference arm is the CPU oracle (plain nested-loop generic join) timed
+on a bounded sample of the outer loop of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2 ** 20
+FLUSH_BYTES = 256 * 2 ** 20
+METRIC = "triangle-count edges/sec (R-MAT scale 22, exact COUNT(*))"
+WORKLOAD = "rmat_s22_ef16 triangle: R-MAT scale 22, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), seed 1505"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="eh", choices=["eh", "reference"])
+    ap.add_argument("--tau", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_src):
+    """DRAM bytes per launch of the count kernel from the committed ncu summary,
+    or None when the summary is missing or was taken on other kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "k_triangle_rmat_s22.md")
+    if not os.path.exists(p):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(p):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("count.cu sha256[:16]") != h:
+        return None
+    try:
+        return float(vals["dram bytes per launch (full size)"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x, world, device=None):
+    """Max over ranks of a float (the slowest rank sets the job's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(edges_per_rank, ms_per_rank_max, world):
+    """Whole-job throughput: all ranks' edges over the slowest rank's time."""
+    return world * edges_per_rank / (ms_per_rank_max / 1e3)
+
+
+def cpu_baseline(g, seconds, seed=7):
+    """The oracle, as it stands, on a bounded sample of the outer loop."""
+    import numpy as np
+    import oracle
+    cores = os.cpu_count() or 1
+    G = oracle.Graph(g["n"], g["src"], g["dst"])
+    rng = np.random.default_rng(seed)
+    verts = rng.permutation(g["n"]).astype(np.uint32)
+    # grow the sample until it has run `seconds`
+    done_edges, t_total, pos, chunk = 0, 0.0, 0, 4096
+    while t_total < seconds and pos < len(verts):
+        part = verts[pos:pos + chunk]
+        t0 = time.perf_counter()
+        _, e = G.triangles_outer(part, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        done_edges += e
+        pos += len(part)
+        chunk = min(chunk * 2, 1 << 20)
+    return {"value": done_edges / t_total, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "sample": "outer-loop vertices %d of %d (random order, seed %d), %d pruned edges, %.1f s; "
+                      "oracle adjacency build excluded" % (pos, g["n"], seed, done_edges, t_total)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import workloads as W
+    g = W.rmat22()
+    import numpy as np
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    G = oracle.Graph(g["n"], g["src"], g["dst"])
+    build_s = time.time() - t0
+    rng = np.random.default_rng(11)
+    verts = rng.permutation(g["n"]).astype(np.uint32)
+    per_step = max(1.0, min(10.0, 120.0 / max(1, args.steps + args.warmup)))
+    # size one step's sample from a probe
+    t0 = time.perf_counter()
+    _, e = G.triangles_outer(verts[:20000], nthreads=cores)
+    probe = time.perf_counter() - t0
+    k = int(min(len(verts), max(1000, 20000 * per_step / max(probe, 1e-3))))
+    pos = 20000
+    for _ in range(args.warmup):
+        G.triangles_outer(verts[pos % len(verts):pos % len(verts) + k], nthreads=cores)
+        pos += k
+    tot_e, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        a = pos % len(verts)
+        part = verts[a:a + k]
+        t0 = time.perf_counter()
+        _, e = G.triangles_outer(part, nthreads=cores)
+        tot_t += time.perf_counter() - t0
+        tot_e += e
+        pos += k
+    value = tot_e / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_vertices": g["n"],
+                                              "sample_outer_vertices_per_step": k},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d random outer-loop vertices per step of %d; adjacency build %.1f s "
+                                       "excluded" % (k, g["n"], build_s)},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_eh(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_1503_02368_gb300 as eh
+    from synth import workloads as W
+
+    g = W.rmat22()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))["rmat_s22_ef16"]
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=args.tau)
+    st = trie.stats()
+    m = st["n_edges"]
+    info = trie.info("triangle")
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    for _ in range(args.warmup):
+        trie.count_async("triangle", out.data_ptr(), stream=stream)
+    torch.cuda.synchronize()
+    trie.status(stream)
+    if world > 1:
+        torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    for k in range(args.steps):
+        flush.fill_(k)                      # L2 flush (256 MiB write) outside the timed interval
+        evs[k][0].record(stream)
+        trie.count_async("triangle", out.data_ptr(), stream=stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    trie.status(stream)
+    count = int(out.item())
+    exact = count == gold["triangle"]
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = reduce_max(ms, world, dev)
+    value = aggregate(m, ms_max, world)
+
+    hbm, peak_kind = measured_peaks()
+    achieved = info["alg_bytes"] / (ms / 1e3) / 1e9
+    traffic = profile_traffic(os.path.join(ROOT, "paper_1503_02368_gb300", "csrc", "count.cu"))
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+            "alg_bytes_per_launch": info["alg_bytes"], "kernel": "k_triangle<0,8>"}
+
+    e2e = None
+    if not args.no_e2e:
+        # the public API end to end: host edge list (pinned) in, count out
+        src_p = torch.from_numpy(g["src"]).pin_memory()
+        dst_p = torch.from_numpy(g["dst"]).pin_memory()
+        ns, nd = src_p.numpy(), dst_p.numpy()
+        e2e_steps = max(2, min(5, args.steps))
+        eh.Trie(ns, nd, g["n"], tau=args.tau).count("triangle")     # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok = True
+        for _ in range(e2e_steps):
+            t = eh.Trie(ns, nd, g["n"], tau=args.tau)
+            ok &= t.count("triangle") == gold["triangle"]
+            t.close()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        e2e_ms = reduce_max(e2e_ms, world, dev)
+        e2e = {"value": aggregate(m, e2e_ms, world), "unit": "edges/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(ns.nbytes + nd.nbytes), "d2h_bytes_per_step": 8, "exact": bool(ok),
+               "includes": "H2D of the raw edge list, trie build (sort, dedup, ordering, layouts), work plan, "
+                           "count, D2H of the count, trie release"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(g, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_vertices": g["n"], "m_unique_edges": m, "tau": args.tau,
+                           "count": count, "exact_vs_oracle": exact,
+                           "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                           "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 2 * args.steps,
+                "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)}}
+        print(json.dumps(line), flush=True)
+    trie.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_eh(args)
+
+
+if __name__ == "__main__":
+    main()

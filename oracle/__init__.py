@@ -51,6 +51,8 @@ def lib():
             f.restype = ctypes.c_uint64
             f.argtypes = [vp, ctypes.c_int, ip]
         L.oracle_vertex_triangles.argtypes = [vp, u32p, ctypes.c_uint64, u64p]
+        L.oracle_triangles_outer.restype = ctypes.c_uint64
+        L.oracle_triangles_outer.argtypes = [vp, u32p, ctypes.c_uint64, ctypes.c_int, u64p, ip]
         L.oracle_induced.restype = vp
         L.oracle_induced.argtypes = [vp, u32p, ctypes.c_uint64]
         L.oracle_layout_is_bitset.restype = ctypes.c_int
@@ -129,6 +131,16 @@ class Graph:
     def triangles(self, pruned=True, nthreads=1):
         o = ctypes.c_int(0)
         return self._chk(lib().oracle_triangles(self._h, int(pruned), _threads(nthreads), ctypes.byref(o)), o)
+
+    def triangles_outer(self, verts, nthreads=1):
+        """Pruned triangle loop nest over the listed outer vertices only:
+        returns (count, pruned edges covered)."""
+        verts = np.ascontiguousarray(verts, np.uint32)
+        o = ctypes.c_int(0)
+        e = ctypes.c_uint64(0)
+        c = lib().oracle_triangles_outer(self._h, _u32p(verts), len(verts), _threads(nthreads), ctypes.byref(e),
+                                         ctypes.byref(o))
+        return self._chk(c, o), int(e.value)
 
     def clique4(self, pruned=True, nthreads=1):
         o = ctypes.c_int(0)

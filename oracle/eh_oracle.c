@@ -227,6 +227,36 @@ uint64_t oracle_triangles(void *h, int pruned, int nthreads, int *overflow) {
     return acc_total(acc, nthreads < 1 ? 1 : nthreads > ORC_MAXT ? ORC_MAXT : nthreads, overflow);
 }
 
+/* The same loop nest restricted to the listed outer vertices x (a sample of
+ * the outer loop, used to time the oracle on a bounded share of a large
+ * graph).  *edges gets the number of pruned edges (x, y) the sample covers. */
+typedef struct { const oracle_graph *g; const uint32_t *verts; orc_acc *acc; orc_acc *edges; } tri_s_ctx;
+
+static void tri_sample_one(void *p, int64_t i, int tid) {
+    tri_s_ctx *c = (tri_s_ctx *)p;
+    uint32_t x = c->verts[i];
+    uint64_t nx;
+    const uint32_t *Nx = set_of(c->g, x, 1, &nx);
+    acc_add(&c->edges[tid], nx);
+    for (uint64_t k = 0; k < nx; ++k) {
+        uint64_t ny;
+        const uint32_t *Ny = set_of(c->g, Nx[k], 1, &ny);
+        acc_add(&c->acc[tid], merge_count(Nx, nx, Ny, ny));
+    }
+}
+
+uint64_t oracle_triangles_outer(void *h, const uint32_t *verts, uint64_t k, int nthreads, uint64_t *edges,
+                                int *overflow) {
+    orc_acc acc[ORC_MAXT], ed[ORC_MAXT];
+    memset(acc, 0, sizeof(acc));
+    memset(ed, 0, sizeof(ed));
+    tri_s_ctx c = {(oracle_graph *)h, verts, acc, ed};
+    orc_for(nthreads, (int64_t)k, tri_sample_one, &c);
+    int nt = nthreads < 1 ? 1 : nthreads > ORC_MAXT ? ORC_MAXT : nthreads;
+    if (edges) *edges = acc_total(ed, nt, NULL);
+    return acc_total(acc, nt, overflow);
+}
+
 /* ------------------------------------------------------------ 4-clique
  * Table 1's 4Clique(x,y,z,w) on the pruned relation, attribute order
  * x > y > z > w (single-node GHD, Sec. 5.2.2): for x; for y in N+(x);

@@ -1,0 +1,46 @@
+"""Host logic of the multi-rank benchmark path, on CPU with gloo (2 ranks)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = [12.0, 15.0][rank]
+    mx = bench.reduce_max(ms, world)
+    val = bench.aggregate(1000.0, mx, world)
+    q.put((rank, mx, val))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_aggregate():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in ps:
+        p.join(timeout=60)
+    assert [r[1] for r in res] == [15.0, 15.0]                 # the slowest rank's time
+    assert all(abs(r[2] - 2 * 1000.0 / 0.015) < 1e-6 for r in res)   # both replicas' edges
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.reduce_max(3.5, 1) == 3.5
+    assert bench.aggregate(10.0, 1000.0, 1) == 10.0

@@ -238,3 +238,16 @@ def test_empty_graph():
     assert g.m == 0 and g.triangles() == 0 and g.clique4() == 0 and g.lollipop() == 0
     g0 = oracle.Graph(0, np.zeros(0, np.uint32), np.zeros(0, np.uint32))
     assert g0.triangles() == 0
+
+
+def test_outer_sample_sums_to_whole():
+    rng = np.random.default_rng(21)
+    n = 60
+    e = G.random_graph(n, 0.3, rng)
+    g = og(n, e)
+    verts = np.arange(n, dtype=np.uint32)
+    half = verts[::2], verts[1::2]
+    c0, e0 = g.triangles_outer(half[0], nthreads=2)
+    c1, e1 = g.triangles_outer(half[1])
+    assert c0 + c1 == g.triangles() == G.bf_triangles(G.adjacency(n, e))
+    assert e0 + e1 == g.m

@@ -67,6 +67,13 @@ bool valid_pattern(int p) { return p >= EH_TRIANGLE && p <= EH_LOLLIPOP_DISTINCT
 
 }  // namespace
 
+eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
+                           unsigned long long *d_out) {
+    return enqueue_count(t, pattern, xo, s, d_out);
+}
+
+eh_status eh_check_status(eh_trie *t, cudaStream_t s) { return check_status(t, s); }
+
 void eh_set_error(const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);

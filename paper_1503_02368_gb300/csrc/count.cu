@@ -262,6 +262,116 @@ __device__ void light_vertex(const TrieView &tv, uint32_t u, uint32_t ratio, Acc
     }
 }
 
+// ------------------------------------------------------------ heavy items
+//
+// A heavy vertex gets the whole CTA: A = N+(u) is staged once (bitset words
+// copied by cp.async.bulk, or a bitmap built from the uint array when its
+// range fits, or the sorted array copied by cp.async.bulk), then the warps
+// take the v = A[j] dynamically through a shared counter.
+
+struct StagedA {
+    const uint32_t *Ag;   // A in global memory
+    const uint32_t *A;    // A as a sorted array (shared or global) when amode != 0
+    uint32_t len, a_lo, a_nw;
+    int amode;            // 0 bitmap in shared memory, 1 sorted in shared memory, 2 sorted in global memory
+};
+
+// Returns false when the bounded wait for the bulk copy ran out (every thread
+// of the CTA then returns false; the caller must leave the kernel).
+template <int WARPS>
+__device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du, uint32_t *sA, uint64_t *mbar,
+                                          uint32_t &phase, StagedA &st, uint32_t *status) {
+    const int tid = threadIdx.x;
+    st.len = du.len;
+    st.Ag = tv.nbr + du.off;
+    const uint32_t first = __ldg(&st.Ag[0]), last = __ldg(&st.Ag[st.len - 1]);
+    st.a_lo = (first >> 7) << 2;
+    st.a_nw = (((last >> 5) + 1 - st.a_lo) + 3) & ~3u;
+    bool copy = false;
+    if (du.nwords && du.nwords <= BM_CAP_WORDS) {
+        st.amode = 0;
+        st.a_lo = du.lo_word;
+        st.a_nw = du.nwords;
+        copy = true;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mbar, st.a_nw * 4);
+            bulk_g2s(sA, tv.words + du.woff, st.a_nw * 4, mbar);
+        }
+    } else if (st.a_nw <= BM_CAP_WORDS) {
+        st.amode = 0;
+        for (uint32_t i = tid * 4; i < st.a_nw; i += WARPS * 128)
+            *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        for (uint32_t i = tid; i < st.len; i += WARPS * 32) {
+            uint32_t x = __ldg(&st.Ag[i]);
+            atomicOr(&sA[(x >> 5) - st.a_lo], 1u << (x & 31));
+        }
+    } else if (st.len <= BM_CAP_WORDS) {
+        st.amode = 1;
+        copy = true;
+        if (tid == 0) {
+            uint32_t bytes = ((st.len + 3) & ~3u) * 4;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mbar, bytes);
+            bulk_g2s(sA, st.Ag, bytes, mbar);
+        }
+    } else {
+        st.amode = 2;
+    }
+    if (copy) {
+        bool ok = mbar_wait(mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
+            mbar_wait(mbar, phase ^ 1);   // drain the copy still in flight, bounded
+            return false;
+        }
+    } else {
+        __syncthreads();
+    }
+    st.A = st.amode == 2 ? st.Ag : sA;
+    return true;
+}
+
+__device__ __forceinline__ uint32_t next_j(uint32_t *s_next) {
+    uint32_t j = 0;
+    if ((threadIdx.x & 31) == 0) j = atomicAdd(s_next, 1u);
+    return __shfl_sync(FULL, j, 0);
+}
+
+template <int MODE, int WARPS>
+__device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32_t ratio, uint32_t *sA,
+                                          uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
+                                          uint32_t *status, unsigned long long *vt) {
+    const int lane = threadIdx.x & 31;
+    const SetDesc du = tv.desc[u];
+    if (threadIdx.x == 0) *s_next = 1;
+    StagedA st;
+    if (!stage_set<WARPS>(tv, du, sA, mbar, phase, st, status)) return false;
+    for (;;) {
+        const uint32_t j = next_j(s_next);
+        if (j >= st.len) break;
+        const uint32_t v = st.amode == 0 ? __ldg(&st.Ag[j]) : st.A[j];
+        const SetDesc dv = tv.desc[v];
+        if (dv.len == 0) continue;
+        const uint32_t duv = du.deg + dv.deg;
+        unsigned long long t0 = acc.t;
+        if (st.amode == 0) pair_bitmap<MODE>(tv, sA, st.a_lo, st.a_nw, dv, duv, acc, vt);
+        else pair_sorted<MODE>(tv, st.A, j, dv, duv, ratio, acc, vt);
+        if (MODE == M_VERTEX) {
+            unsigned long long pc = acc.t - t0;
+            for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
+            if (lane == 0 && pc) {
+                atomicAdd(&vt[u], pc);
+                atomicAdd(&vt[v], pc);
+            }
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 // counters[0]: next heavy item, counters[1]: next light chunk
 template <int MODE, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint32_t *__restrict__ heavy, uint32_t n_heavy,
@@ -272,7 +382,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
     extern __shared__ __align__(16) uint32_t sA[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_item, s_next;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     Acc acc{0, 0};
     uint32_t phase = 0;
     if (tid == 0) mbar_init(&mbar, 1);
@@ -284,79 +394,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
-        const uint32_t u = heavy[item];
-        const SetDesc du = tv.desc[u];
-        const uint32_t len = du.len;
-        const uint32_t *Ag = tv.nbr + du.off;
-        const uint32_t first = __ldg(&Ag[0]), last = __ldg(&Ag[len - 1]);
-        // on-chip form of A
-        uint32_t a_lo = (first >> 7) << 2;
-        uint32_t a_nw = (((last >> 5) + 1 - a_lo) + 3) & ~3u;
-        int amode;   // 0 bitmap, 1 sorted in shared memory, 2 sorted in global memory
-        if (du.nwords && du.nwords <= BM_CAP_WORDS) {
-            amode = 0;
-            a_lo = du.lo_word;
-            a_nw = du.nwords;
-            if (tid == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&mbar, a_nw * 4);
-                bulk_g2s(sA, tv.words + du.woff, a_nw * 4, &mbar);
-            }
-        } else if (a_nw <= BM_CAP_WORDS) {
-            amode = 0;
-            for (uint32_t i = tid * 4; i < a_nw; i += WARPS * 128)
-                *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
-            __syncthreads();
-            for (uint32_t i = tid; i < len; i += WARPS * 32) {
-                uint32_t x = __ldg(&Ag[i]);
-                atomicOr(&sA[(x >> 5) - a_lo], 1u << (x & 31));
-            }
-        } else if (len <= BM_CAP_WORDS) {
-            amode = 1;
-            if (tid == 0) {
-                uint32_t bytes = ((len + 3) & ~3u) * 4;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&mbar, bytes);
-                bulk_g2s(sA, Ag, bytes, &mbar);
-            }
-        } else {
-            amode = 2;
-        }
-        if (tid == 0) s_next = 1;
-        if ((du.nwords && du.nwords <= BM_CAP_WORDS) || amode == 1) {
-            bool ok = mbar_wait(&mbar, phase);
-            phase ^= 1;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
-                mbar_wait(&mbar, phase ^ 1);   // drain the copy still in flight, bounded
-                return;
-            }
-        } else {
-            __syncthreads();
-        }
-        const uint32_t *A = amode == 2 ? Ag : sA;
-        for (;;) {
-            uint32_t j = 0;
-            if (lane == 0) j = atomicAdd(&s_next, 1u);
-            j = __shfl_sync(FULL, j, 0);
-            if (j >= len) break;
-            const uint32_t v = amode == 0 ? __ldg(&Ag[j]) : A[j];
-            const SetDesc dv = tv.desc[v];
-            if (dv.len == 0) continue;
-            const uint32_t duv = du.deg + dv.deg;
-            unsigned long long t0 = acc.t;
-            if (amode == 0) pair_bitmap<MODE>(tv, sA, a_lo, a_nw, dv, duv, acc, vt);
-            else pair_sorted<MODE>(tv, A, j, dv, duv, ratio, acc, vt);
-            if (MODE == M_VERTEX) {
-                unsigned long long pc = acc.t - t0;
-                for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
-                if (lane == 0 && pc) {
-                    atomicAdd(&vt[u], pc);
-                    atomicAdd(&vt[v], pc);
-                }
-            }
-        }
-        __syncthreads();
+        if (!tri_heavy<MODE, WARPS>(tv, heavy[item], ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
     }
 
     // light vertices: one warp each, taken 32 at a time
@@ -382,9 +420,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
             if (old + s < old) atomicOr(status, DEV_ST_OVERFLOW);
         }
     }
-    (void)warp;
 }
-
 
 // ------------------------------------------------------------------ 4-clique
 //
@@ -551,6 +587,62 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
 }
 
 template <int WARPS>
+__device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_t ratio, uint32_t *sA, uint32_t *sS,
+                                         uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
+                                         uint32_t *status, uint32_t *arena, uint64_t arena_per_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
+    const SetDesc dx = tv.desc[x];
+    if (threadIdx.x == 0) *s_next = 2;
+    StagedA st;
+    if (!stage_set<WARPS>(tv, dx, sA, mbar, phase, st, status)) return false;
+    for (;;) {
+        const uint32_t j = next_j(s_next);
+        if (j >= st.len) break;
+        const uint32_t y = st.amode == 0 ? __ldg(&st.Ag[j]) : st.A[j];
+        const SetDesc dy = tv.desc[y];
+        if (dy.len < 2) continue;
+        const uint32_t bound = min(j, dy.len);
+        uint32_t *S = bound <= S_CAP ? sS + warp * S_CAP : arena + gwarp * arena_per_warp;
+        if (bound > S_CAP && (arena == nullptr || bound > arena_per_warp)) {
+            if (lane == 0) atomicOr(status, DEV_ST_INVALID);
+            continue;
+        }
+        uint32_t ns = st.amode == 0 ? emit_bitmap(tv, sA, st.a_lo, st.a_nw, dy, S)
+                                    : emit_sorted(tv, st.A, j, dy, ratio, S);
+        clique_level2(tv, S, ns, ratio, acc);
+        __syncwarp();
+    }
+    __syncthreads();
+    return true;
+}
+
+// light vertex x: A and S held one element per lane
+__device__ void k4_light(const TrieView &tv, uint32_t x, uint32_t ratio, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const SetDesc dx = tv.desc[x];
+    const uint32_t k = dx.len;
+    const uint32_t a = lane < k ? __ldg(&tv.nbr[dx.off + lane]) : EH_PAD;
+    for (uint32_t j = 2; j < k; ++j) {
+        const uint32_t y = __shfl_sync(FULL, a, j);
+        const SetDesc dy = tv.desc[y];
+        if (dy.len < 2) continue;
+        const uint32_t m = __ballot_sync(FULL, light_match(tv, a, j, dy, ratio));
+        const uint32_t ns = __popc(m);
+        if (ns < 2) continue;
+        const uint32_t src = (uint32_t)lane < ns ? nth_set_bit(m, lane) : 0u;
+        uint32_t sv = __shfl_sync(FULL, a, src);
+        if ((uint32_t)lane >= ns) sv = EH_PAD;
+        for (uint32_t i = 1; i < ns; ++i) {
+            const uint32_t z = __shfl_sync(FULL, sv, i);
+            const SetDesc dz = tv.desc[z];
+            if (dz.len == 0) continue;
+            if (light_match(tv, sv, i, dz, ratio)) acc.t += 1;
+        }
+    }
+}
+
+template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint32_t *__restrict__ heavy, uint32_t n_heavy,
                                                         const uint32_t *__restrict__ light, uint32_t n_light,
                                                         uint32_t ratio, unsigned long long *counters,
@@ -561,93 +653,102 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
     uint32_t *sS = smem + BM_CAP_WORDS;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_item, s_next;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
+    const int tid = threadIdx.x, lane = tid & 31;
     Acc acc{0, 0};
     uint32_t phase = 0;
     if (tid == 0) mbar_init(&mbar, 1);
     __syncthreads();
-
     for (;;) {
         if (tid == 0) s_item = (uint32_t)min((unsigned long long)n_heavy, atomicAdd(&counters[0], 1ull));
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
-        const uint32_t x = heavy[item];
-        const SetDesc dx = tv.desc[x];
-        const uint32_t len = dx.len;
-        const uint32_t *Ag = tv.nbr + dx.off;
-        const uint32_t first = __ldg(&Ag[0]), last = __ldg(&Ag[len - 1]);
-        uint32_t a_lo = (first >> 7) << 2;
-        uint32_t a_nw = (((last >> 5) + 1 - a_lo) + 3) & ~3u;
-        int amode;
-        bool copy = false;
-        if (dx.nwords && dx.nwords <= BM_CAP_WORDS) {
-            amode = 0;
-            a_lo = dx.lo_word;
-            a_nw = dx.nwords;
-            copy = true;
-            if (tid == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&mbar, a_nw * 4);
-                bulk_g2s(sA, tv.words + dx.woff, a_nw * 4, &mbar);
-            }
-        } else if (a_nw <= BM_CAP_WORDS) {
-            amode = 0;
-            for (uint32_t i = tid * 4; i < a_nw; i += WARPS * 128)
-                *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
-            __syncthreads();
-            for (uint32_t i = tid; i < len; i += WARPS * 32) {
-                uint32_t v = __ldg(&Ag[i]);
-                atomicOr(&sA[(v >> 5) - a_lo], 1u << (v & 31));
-            }
-        } else if (len <= BM_CAP_WORDS) {
-            amode = 1;
-            copy = true;
-            if (tid == 0) {
-                uint32_t bytes = ((len + 3) & ~3u) * 4;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&mbar, bytes);
-                bulk_g2s(sA, Ag, bytes, &mbar);
-            }
-        } else {
-            amode = 2;
-        }
-        if (tid == 0) s_next = 2;
-        if (copy) {
-            bool ok = mbar_wait(&mbar, phase);
-            phase ^= 1;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
-                mbar_wait(&mbar, phase ^ 1);
-                return;
-            }
-        } else {
-            __syncthreads();
-        }
-        const uint32_t *A = amode == 2 ? Ag : sA;
-        for (;;) {
-            uint32_t j = 0;
-            if (lane == 0) j = atomicAdd(&s_next, 1u);
-            j = __shfl_sync(FULL, j, 0);
-            if (j >= len) break;
-            const uint32_t y = amode == 0 ? __ldg(&Ag[j]) : A[j];
-            const SetDesc dy = tv.desc[y];
-            if (dy.len < 2) continue;
-            const uint32_t bound = min(j, dy.len);
-            uint32_t *S = bound <= S_CAP ? sS + warp * S_CAP : arena + gwarp * arena_per_warp;
-            if (bound > S_CAP && (arena == nullptr || bound > arena_per_warp)) {
-                if (lane == 0) atomicOr(status, DEV_ST_INVALID);
-                continue;
-            }
-            uint32_t ns = amode == 0 ? emit_bitmap(tv, sA, a_lo, a_nw, dy, S) : emit_sorted(tv, A, j, dy, ratio, S);
-            clique_level2(tv, S, ns, ratio, acc);
-            __syncwarp();
-        }
-        __syncthreads();
+        if (!k4_heavy<WARPS>(tv, heavy[item], ratio, sA, sS, &mbar, phase, &s_next, acc, status, arena,
+                             arena_per_warp))
+            return;
     }
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&counters[1], 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= n_light) break;
+        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
+        for (uint32_t it = (uint32_t)base; it < end; ++it) k4_light(tv, __ldg(&light[it]), ratio, acc);
+    }
+    unsigned long long t = acc.t;
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
+    if (lane == 0 && t) atomicAdd(&out[0], t);
+}
 
-    // light vertices: A and S held one element per lane
+// ------------------------------------------------------------------- batch
+//
+// Many queries, each over its own induced sub-trie, in one persistent launch.
+// The sub-tries of a batch are concatenated: sub-vertex s belongs to query
+// q = sub_q[s] and is local vertex s - qbase[q] of it; sets hold local ids.
+// Items (sub-vertices) of every query are mixed, heaviest first; each item
+// runs the triangle, lollipop or 4-clique routine of its query's pattern and
+// adds into out[2q] (triangles or 4-cliques) and out[2q+1] (lollipop sum).
+
+__device__ __forceinline__ TrieView view_of(const BatchView &b, uint32_t q) {
+    TrieView v;
+    const uint32_t base = b.qbase[q];
+    v.desc = b.desc + base;
+    v.nbr = b.nbr;
+    v.words = b.words;
+    v.deg = b.deg + base;
+    v.n = b.qbase[q + 1] - base;
+    return v;
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_batch(BatchView bv, const uint32_t *__restrict__ heavy, uint32_t n_heavy,
+                                                      const uint32_t *__restrict__ light, uint32_t n_light,
+                                                      uint32_t ratio, unsigned long long *counters,
+                                                      unsigned long long *out, uint32_t *status, uint32_t *arena,
+                                                      uint64_t arena_per_warp) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *sA = smem;
+    uint32_t *sS = smem + BM_CAP_WORDS;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_item, s_next;
+    __shared__ unsigned long long red_t[WARPS], red_s[WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t phase = 0;
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) s_item = (uint32_t)min((unsigned long long)n_heavy, atomicAdd(&counters[0], 1ull));
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_heavy) break;
+        const uint32_t sidx = heavy[item];
+        const uint32_t q = bv.sub_q[sidx];
+        const TrieView tv = view_of(bv, q);
+        const uint32_t u = sidx - bv.qbase[q];
+        const uint32_t pat = bv.qpat[q];
+        Acc acc{0, 0};
+        bool ok;
+        if (pat == EH_CLIQUE4)
+            ok = k4_heavy<WARPS>(tv, u, ratio, sA, sS, &mbar, phase, &s_next, acc, status, arena, arena_per_warp);
+        else if (pat == EH_TRIANGLE)
+            ok = tri_heavy<M_COUNT, WARPS>(tv, u, ratio, sA, &mbar, phase, &s_next, acc, status, nullptr);
+        else
+            ok = tri_heavy<M_LOLLI, WARPS>(tv, u, ratio, sA, &mbar, phase, &s_next, acc, status, nullptr);
+        if (!ok) return;
+        unsigned long long t = acc.t, s = acc.s;
+        for (int d = 16; d > 0; d >>= 1) {
+            t += __shfl_xor_sync(FULL, t, d);
+            s += __shfl_xor_sync(FULL, s, d);
+        }
+        if (lane == 0) { red_t[warp] = t; red_s[warp] = s; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long T = 0, S = 0;
+            for (int w = 0; w < WARPS; ++w) { T += red_t[w]; S += red_s[w]; }
+            if (T) atomicAdd(&out[2 * q], T);
+            if (S) atomicAdd(&out[2 * q + 1], S);
+        }
+    }
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&counters[1], 32ull);
@@ -655,33 +756,46 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
         if (base >= n_light) break;
         uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
         for (uint32_t it = (uint32_t)base; it < end; ++it) {
-            const uint32_t x = __ldg(&light[it]);
-            const SetDesc dx = tv.desc[x];
-            const uint32_t k = dx.len;
-            const uint32_t a = lane < k ? __ldg(&tv.nbr[dx.off + lane]) : EH_PAD;
-            for (uint32_t j = 2; j < k; ++j) {
-                const uint32_t y = __shfl_sync(FULL, a, j);
-                const SetDesc dy = tv.desc[y];
-                if (dy.len < 2) continue;
-                const uint32_t m = __ballot_sync(FULL, light_match(tv, a, j, dy, ratio));
-                const uint32_t ns = __popc(m);
-                if (ns < 2) continue;
-                const uint32_t src = (uint32_t)lane < ns ? nth_set_bit(m, lane) : 0u;
-                uint32_t sv = __shfl_sync(FULL, a, src);
-                if ((uint32_t)lane >= ns) sv = EH_PAD;
-                for (uint32_t i = 1; i < ns; ++i) {
-                    const uint32_t z = __shfl_sync(FULL, sv, i);
-                    const SetDesc dz = tv.desc[z];
-                    if (dz.len == 0) continue;
-                    if (light_match(tv, sv, i, dz, ratio)) acc.t += 1;
-                }
+            const uint32_t sidx = __ldg(&light[it]);
+            const uint32_t q = bv.sub_q[sidx];
+            const TrieView tv = view_of(bv, q);
+            const uint32_t u = sidx - bv.qbase[q];
+            const uint32_t pat = bv.qpat[q];
+            Acc acc{0, 0};
+            if (pat == EH_CLIQUE4) k4_light(tv, u, ratio, acc);
+            else if (pat == EH_TRIANGLE) light_vertex<M_COUNT>(tv, u, ratio, acc, nullptr);
+            else light_vertex<M_LOLLI>(tv, u, ratio, acc, nullptr);
+            unsigned long long t = acc.t, s = acc.s;
+            for (int d = 16; d > 0; d >>= 1) {
+                t += __shfl_xor_sync(FULL, t, d);
+                s += __shfl_xor_sync(FULL, s, d);
+            }
+            if (lane == 0) {
+                if (t) atomicAdd(&out[2 * q], t);
+                if (s) atomicAdd(&out[2 * q + 1], s);
             }
         }
     }
+}
 
-    unsigned long long t = acc.t;
-    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
-    if (lane == 0 && t) atomicAdd(&out[0], t);
+template <int WARPS>
+eh_status launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n_heavy, const uint32_t *light,
+                       uint32_t n_light, const eh_exec_opts &xo, cudaStream_t s, unsigned long long *d_out,
+                       unsigned long long *d_counters, uint32_t *d_status, uint32_t *arena, uint64_t per_warp,
+                       uint32_t *grid_warps) {
+    auto kern = k_batch<WARPS>;
+    const int smem = (BM_CAP_WORDS + WARPS * S_CAP) * 4;
+    EH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)(eh_num_sms() * per_sm);
+    if (grid_warps) { *grid_warps = grid * WARPS; return EH_OK; }
+    EH_CUDA_TRY(cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned long long), s));
+    kern<<<grid, WARPS * 32, smem, s>>>(bv, heavy, n_heavy, light, n_light, xo.gallop_ratio, d_counters, d_out,
+                                        d_status, arena, per_warp);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
 }
 
 template <int WARPS>
@@ -774,5 +888,19 @@ eh_status eh_launch_clique4(const eh_trie *t, const WorkPlan &plan, TrieView tv,
         case 4: return launch_k4<4>(tt, plan, tv, xo, s, d_acc, d_counters, d_status);
         case 16: return launch_k4<16>(tt, plan, tv, xo, s, d_acc, d_counters, d_status);
         default: return launch_k4<8>(tt, plan, tv, xo, s, d_acc, d_counters, d_status);
+    }
+}
+
+eh_status eh_launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n_heavy, const uint32_t *light,
+                          uint32_t n_light, const eh_exec_opts &xo, cudaStream_t s, unsigned long long *d_out,
+                          unsigned long long *d_counters, uint32_t *d_status, uint32_t *arena,
+                          uint64_t arena_words_per_warp, uint32_t *grid_warps) {
+    switch (xo.cta_warps) {
+        case 4: return launch_batch<4>(bv, heavy, n_heavy, light, n_light, xo, s, d_out, d_counters, d_status, arena,
+                                       arena_words_per_warp, grid_warps);
+        case 16: return launch_batch<16>(bv, heavy, n_heavy, light, n_light, xo, s, d_out, d_counters, d_status,
+                                         arena, arena_words_per_warp, grid_warps);
+        default: return launch_batch<8>(bv, heavy, n_heavy, light, n_light, xo, s, d_out, d_counters, d_status,
+                                        arena, arena_words_per_warp, grid_warps);
     }
 }

@@ -68,6 +68,17 @@ struct TrieView {
     uint32_t n;
 };
 
+// Concatenated induced sub-tries of a batch of queries (see count.cu).
+struct BatchView {
+    const SetDesc *desc;    // per sub-vertex
+    const uint32_t *nbr;    // sets of local ids
+    const uint32_t *words;  // bitset pool
+    const uint32_t *deg;    // degree in the induced subgraph
+    const uint32_t *sub_q;  // query of each sub-vertex
+    const uint32_t *qbase;  // first sub-vertex of each query (n_queries + 1)
+    const uint32_t *qpat;   // pattern of each query
+};
+
 // per-pattern work lists (vertex ids, heaviest first)
 struct WorkPlan {
     uint32_t light_max = 0;
@@ -168,3 +179,15 @@ eh_status eh_launch_clique4(const eh_trie *t, const WorkPlan &plan, TrieView tv,
                             cudaStream_t s, unsigned long long *d_acc, unsigned long long *d_counters,
                             uint32_t *d_status, uint32_t *d_arena, uint64_t arena_words_per_warp);
 eh_exec_opts eh_exec_defaults(const eh_exec_opts *x);
+// grid_warps != NULL: only reports the warps of the launch (sizes the arena)
+eh_status eh_launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n_heavy, const uint32_t *light,
+                          uint32_t n_light, const eh_exec_opts &xo, cudaStream_t s, unsigned long long *d_out,
+                          unsigned long long *d_counters, uint32_t *d_status, uint32_t *arena,
+                          uint64_t arena_words_per_warp, uint32_t *grid_warps);
+// set-level layouts of a pruned trie given as padded uint arrays (trie_build.cu)
+eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint32_t *len, const uint32_t *deg,
+                           uint32_t nv, uint32_t tau, uint32_t min_len, cudaStream_t s, SetDesc *desc_out,
+                           uint32_t **words_out, uint64_t *n_words_out, uint64_t *n_bitset_out);
+eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
+                           unsigned long long *d_out);
+eh_status eh_check_status(eh_trie *t, cudaStream_t s);

@@ -407,6 +407,41 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
 
 }  // namespace
 
+// Set-level layouts (Sec. 4.4) for a pruned trie given as padded uint
+// arrays: decides bitset/uint per set, fills the bitset pool and the
+// descriptors.  Used for the induced sub-tries of query batches.
+eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint32_t *len, const uint32_t *deg,
+                           uint32_t nv, uint32_t tau, uint32_t min_len, cudaStream_t s, SetDesc *desc_out,
+                           uint32_t **words_out, uint64_t *n_words_out, uint64_t *n_bitset_out) {
+    *words_out = nullptr;
+    *n_words_out = 0;
+    Temps tmp(s);
+    uint64_t *nwords = nullptr, *woff = nullptr;
+    uint32_t *lo_word = nullptr;
+    EH_TRY(tmp.alloc(&nwords, (uint64_t)nv + 1));
+    EH_TRY(tmp.alloc(&woff, (uint64_t)nv + 1));
+    EH_TRY(tmp.alloc(&lo_word, (uint64_t)nv + 1));
+    EH_CUDA_TRY(cudaMemsetAsync(nwords, 0, ((uint64_t)nv + 1) * 8, s));
+    if (nv) k_layout<<<blocks_for(nv), 256, 0, s>>>(nbr, off, len, nv, tau, min_len, nwords, lo_word);
+    uint64_t tw = 0;
+    EH_TRY(dev_exclusive_scan_u64(nwords, woff, (uint64_t)nv + 1, s, &tw));
+    uint32_t *words = nullptr;
+    EH_TRY(dev_alloc(&words, tw, s));
+    EH_CUDA_TRY(cudaMemsetAsync(words, 0, (tw ? tw : 1) * 4, s));
+    if (nv) k_fill_bits<<<blocks_for(nv, 8), 256, 0, s>>>(nbr, off, len, nwords, woff, lo_word, nv, words);
+    if (nv) k_desc<<<blocks_for(nv), 256, 0, s>>>(off, len, deg, nwords, woff, lo_word, nv, desc_out);
+    if (n_bitset_out) *n_bitset_out = 0;   // not tracked for sub-tries
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        dev_free(words, s);
+        eh_set_error("layouts: %s", cudaGetErrorString(e));
+        return EH_ECUDA;
+    }
+    *words_out = words;
+    *n_words_out = tw;
+    return EH_OK;
+}
+
 extern "C" eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uint64_t n_edges, uint32_t n_vertices,
                                    const eh_build_opts *opts, void *stream, eh_trie **out) {
     if (!out) { eh_set_error("eh_build_trie: out is NULL"); return EH_EINVAL; }

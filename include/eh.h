@@ -212,14 +212,22 @@ typedef struct {
 
 eh_status eh_server_create(const eh_trie *trie, uint64_t memory_budget_bytes, uint32_t max_batch,
                            uint32_t max_inflight, eh_server **out);
-/* Copies subset[0..subset_len) and queues the query; *ticket identifies it. */
+/* Copies subset[0..subset_len) and queues the query; *ticket identifies it.
+ * EH_EBUSY when the query's estimated device footprint does not fit the
+ * budget next to the queries admitted and not yet finished. */
 eh_status eh_server_submit(eh_server *s, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
                            uint64_t *ticket);
-/* 1 if done (result in *count, *status), 0 if pending; EH_EINVAL for an unknown ticket. */
+/* *done = 1 when the result is ready (then in *count, *status; results stay
+ * available until eh_server_destroy), 0 while pending; EH_EINVAL for an
+ * unknown ticket. */
 eh_status eh_server_poll(eh_server *s, uint64_t ticket, int *done, uint64_t *count, eh_status *status);
-/* Blocks up to timeout_ms (0 = no limit) for the ticket. */
+/* Blocks up to timeout_ms (0 = no limit) for the ticket; EH_ETIMEOUT when
+ * the limit passes first. */
 eh_status eh_server_wait(eh_server *s, uint64_t ticket, uint32_t timeout_ms, uint64_t *count,
                          eh_status *status);
+/* Seconds from the ticket's submit() to its result reaching the host
+ * (measured by the server; EH_EINVAL while the ticket is not complete). */
+eh_status eh_server_latency(eh_server *s, uint64_t ticket, double *seconds);
 eh_status eh_server_stats_get(eh_server *s, eh_server_stats *out);
 void eh_server_destroy(eh_server *s);
 

@@ -113,6 +113,7 @@ struct eh_trie {
     uint64_t n_bitset = 0, n_nonempty = 0;
     double density_skew = 0;
     uint64_t device_bytes = 0;
+    std::vector<uint32_t> h_out_by_old;   // |N+(v)| by original id (host; serving footprints)
 
     // scratch owned by the trie: counters, accumulators, status
     unsigned long long *d_scratch = nullptr;  // 16 words

@@ -369,9 +369,10 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     if (n) k_desc<<<blocks_for(n), 256, 0, s>>>(ooff, odeg, t->d_deg, nwords, woff, lo_word, n, t->d_desc);
 
     // stats (host side, diagnostics only)
-    std::vector<uint32_t> hdeg(n), hodeg(n);
+    std::vector<uint32_t> hdeg(n), hodeg(n), hn2o(n);
     std::vector<uint64_t> hnw(n);
     if (n) {
+        EH_CUDA_TRY(cudaMemcpyAsync(hn2o.data(), t->d_new2old, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
         EH_CUDA_TRY(cudaMemcpyAsync(hdeg.data(), t->d_deg, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
         EH_CUDA_TRY(cudaMemcpyAsync(hodeg.data(), odeg, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
         EH_CUDA_TRY(cudaMemcpyAsync(hnw.data(), nwords, (uint64_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -391,6 +392,8 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
         sum2 += (double)hdeg[v] * hdeg[v];
         hist[hdeg[v]]++;
     }
+    t->h_out_by_old.assign(n, 0);
+    for (uint32_t v = 0; v < n; ++v) t->h_out_by_old[hn2o[v]] = hodeg[v];
     t->n_active = act;
     t->max_out = mo;
     t->n_bitset = nbs;

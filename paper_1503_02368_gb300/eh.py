@@ -59,7 +59,7 @@ class ServerStats(ctypes.Structure):
 EXPORTED = ["eh_build_trie", "eh_count", "eh_count_ex", "eh_count_async", "eh_count_status", "eh_count_info_get",
             "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_trie_stats_get", "eh_trie_export",
             "eh_free_trie", "eh_last_error", "eh_server_create", "eh_server_submit", "eh_server_poll",
-            "eh_server_wait", "eh_server_stats_get", "eh_server_destroy"]
+            "eh_server_wait", "eh_server_latency", "eh_server_stats_get", "eh_server_destroy"]
 
 
 def library_path():
@@ -112,6 +112,8 @@ def lib():
     L.eh_server_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), u64p, ctypes.POINTER(ctypes.c_int)]
     L.eh_server_wait.restype = st
     L.eh_server_wait.argtypes = [vp, u64, u32, u64p, ctypes.POINTER(ctypes.c_int)]
+    L.eh_server_latency.restype = st
+    L.eh_server_latency.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_double)]
     L.eh_server_stats_get.restype = st
     L.eh_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
     L.eh_server_destroy.restype = None
@@ -295,6 +297,11 @@ class Server:
         cnt, st = ctypes.c_uint64(0), ctypes.c_int(0)
         _check(lib().eh_server_wait(self._h, ticket, timeout_ms, ctypes.byref(cnt), ctypes.byref(st)))
         return int(cnt.value), int(st.value)
+
+    def latency(self, ticket):
+        x = ctypes.c_double(0)
+        _check(lib().eh_server_latency(self._h, ticket, ctypes.byref(x)))
+        return float(x.value)
 
     def stats(self):
         s = ServerStats()

@@ -60,6 +60,24 @@ def main():
         out[name] = rec
         print(name, {k: v for k, v in rec.items() if k != "vertex_triangles"}, "%.1fs" % (time.time() - t0),
               flush=True)
+    # the 4,096-query ego-net batch: expected counts of a sample of queries
+    t0 = time.time()
+    g = W.rmat20_ego_batch()
+    G = oracle.Graph(g["n"], g["src"], g["dst"])
+    off, pool, pq = g["offsets"], g["pool"], g["patterns"]
+    sizes = np.diff(off)
+    rng = np.random.default_rng(4)
+    sample = sorted(set(range(8)) | set(rng.choice(len(pq), 56, replace=False).tolist()) |
+                    set(np.argsort(-sizes)[:4].tolist()))
+    rec = {"n": g["n"], "fingerprint": fingerprint(g), "n_queries": len(pq),
+           "subset_fingerprint": __import__("hashlib").sha256(pool.tobytes() + off.tobytes()).hexdigest()[:32],
+           "queries": {}}
+    for q in sample:
+        pat = "clique4" if pq[q] else "triangle"
+        rec["queries"][int(q)] = {"pattern": pat, "size": int(sizes[q]),
+                                  "count": G.induced(pool[off[q]:off[q + 1]]).count(pat, nthreads=T)}
+    out["rmat_s20_ego4096"] = rec
+    print("rmat_s20_ego4096", len(sample), "queries", "%.1fs" % (time.time() - t0), flush=True)
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "workload_counts.json"), "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
 

@@ -141,6 +141,27 @@ eh_status eh_count_async(const eh_trie *trie, eh_pattern pattern, const eh_exec_
  * status word of the trie's last asynchronous counts (then clears it). */
 eh_status eh_count_status(const eh_trie *trie, void *stream);
 
+/* eh_count_noalloc -- a whole-graph count (as eh_count) that allocates
+ * nothing.  For callers that may not allocate device memory while they
+ * count: a process that has handed its device memory to a fixed pool or
+ * budget, code running where an allocation could block or fail at the wrong
+ * moment.  The paper has no counterpart: this is a property of this library.
+ *   trie       a trie built by eh_build_trie whose work plan exists: call
+ *              eh_count_info_get (or any whole-graph count) on it once first,
+ *              otherwise EH_EINVAL.
+ *   out_count  host uint64, written on success.  The call synchronises `stream`.
+ * Scratch (work counters, accumulators, status word and the 4-clique spill
+ * arena) lives in one 32 MiB static device array that every device using the
+ * library keeps until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current.
+ * The 4-clique pattern needs max out-degree x launch warps x 4 bytes of arena
+ * when the max out-degree exceeds 1024; above 32 MiB the call returns
+ * EH_EINVAL with the sizes in eh_last_error, before launching anything.
+ * All calls share the array (each clears its counters first): calls whose
+ * work overlaps on the GPU, on any trie or stream, race and must not be
+ * issued. */
+eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, void *stream, uint64_t *out_count);
+
 /* eh_count_info_get -- work-plan facts of a whole-graph count (builds the
  * plan if needed): alg_bytes = the bytes the method must move in one pass
  * (staged sets once per vertex; per intersection the stored layout's bytes

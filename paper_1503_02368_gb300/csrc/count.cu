@@ -904,3 +904,138 @@ eh_status eh_launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n
                                         arena, arena_words_per_warp, grid_warps);
     }
 }
+
+// ------------------------------------------ whole-graph count without allocation
+//
+// eh_count_noalloc runs the same count kernels as eh_count, but keeps their
+// scratch (the work-distribution counters, the accumulators, the status word
+// and the 4-clique spill arena) in the file-scope array below instead of
+// memory it allocates.  The array is a fixed 32 MiB that every device using
+// this library holds until the process exits.
+
+namespace {
+
+constexpr uint64_t NOALLOC_WORDS = 8ull << 20;   // 32 MiB of 32-bit words
+constexpr uint64_t NOALLOC_HEAD = 64;            // counters, accumulators, status; arena after
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (the name is only a host-side stand-in for it).
+eh_status noalloc_scratch(uint32_t **out) {
+    int dev = 0;
+    EH_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) { eh_set_error("eh_count_noalloc: device ordinal %d out of range", dev); return EH_EINVAL; }
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            eh_set_error("eh_count_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return EH_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (uint32_t *)g_noalloc_addr[dev];
+    return EH_OK;
+}
+
+__global__ void k_noalloc_finalize(const unsigned long long *acc, int pattern, unsigned long long *out,
+                                   uint32_t *status) {
+    const unsigned long long T = acc[0], S = acc[1], K = acc[2];
+    unsigned long long r = 0;
+    switch (pattern) {
+        case EH_TRIANGLE: r = T; break;
+        case EH_CLIQUE4: r = K; break;
+        case EH_LOLLIPOP:
+            if (S >> 63) atomicOr(status, DEV_ST_OVERFLOW);
+            r = 2ull * S;
+            break;
+        default: r = S - 6ull * T; break;
+    }
+    *out = r;
+}
+
+}  // namespace
+
+extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, void *stream, uint64_t *out_count) {
+    if (!trie || !out_count) { eh_set_error("eh_count_noalloc: NULL argument"); return EH_EINVAL; }
+    if (pattern < EH_TRIANGLE || pattern > EH_LOLLIPOP_DISTINCT) {
+        eh_set_error("eh_count_noalloc: unknown pattern %d", (int)pattern);
+        return EH_EINVAL;
+    }
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    const eh_exec_opts xo = eh_exec_defaults(nullptr);
+    const WorkPlan *plan = nullptr;
+    {
+        std::lock_guard<std::mutex> g(t->mu);
+        auto it = t->plans.find(xo.light_max);
+        if (it != t->plans.end()) plan = &it->second;
+    }
+    if (!plan) {
+        eh_set_error("eh_count_noalloc: the trie has no work plan yet; call eh_count_info_get (or any "
+                     "whole-graph count) on it once first");
+        return EH_EINVAL;
+    }
+    uint32_t *scr = nullptr;
+    EH_TRY(noalloc_scratch(&scr));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *counters = (unsigned long long *)scr;       // words 0..3
+    unsigned long long *acc = (unsigned long long *)(scr + 4);      // words 4..9: T, S, K
+    unsigned long long *res = (unsigned long long *)(scr + 10);     // words 10..11: the count
+    uint32_t *status = scr + 12;
+    uint32_t *arena = scr + NOALLOC_HEAD;
+    const uint64_t arena_cap = NOALLOC_WORDS - NOALLOC_HEAD;
+    const TrieView tv = t->view();
+
+    auto kern4 = k_clique4<8>;
+    const int smem4 = (BM_CAP_WORDS + 8 * S_CAP) * 4;
+    unsigned grid4 = 0;
+    uint64_t per_warp = 0;
+    if (pattern == EH_CLIQUE4) {
+        EH_CUDA_TRY(cudaFuncSetAttribute(kern4, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4));
+        int per_sm = 0;
+        EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern4, 8 * 32, smem4));
+        grid4 = (unsigned)(eh_num_sms() * (per_sm < 1 ? 1 : per_sm));
+        if (t->max_out > S_CAP) {
+            per_warp = ((uint64_t)t->max_out + 3) & ~3ull;
+            const uint64_t need = per_warp * grid4 * 8;
+            if (need > arena_cap) {
+                eh_set_error("eh_count_noalloc: the 4-clique spill arena needs %llu bytes (max out-degree %u, %u "
+                             "warps) but the static scratch holds %llu; use eh_count",
+                             (unsigned long long)(need * 4), t->max_out, grid4 * 8,
+                             (unsigned long long)(arena_cap * 4));
+                return EH_EINVAL;
+            }
+        }
+    }
+    // the array keeps the previous call's contents: clear what must start at zero
+    EH_CUDA_TRY(cudaMemsetAsync(scr, 0, NOALLOC_HEAD * 4, s));
+    if (pattern == EH_CLIQUE4) {
+        kern4<<<grid4, 8 * 32, smem4, s>>>(tv, plan->d_heavy, plan->n_heavy, plan->d_light, plan->n_light,
+                                           xo.gallop_ratio, counters, acc + 2, status,
+                                           per_warp ? arena : nullptr, per_warp);
+    } else {
+        auto kern = pattern == EH_TRIANGLE ? k_triangle<M_COUNT, 8> : k_triangle<M_LOLLI, 8>;
+        const int smem = BM_CAP_WORDS * 4;
+        int per_sm = 0;
+        EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 8 * 32, smem));
+        unsigned grid = (unsigned)(eh_num_sms() * (per_sm < 1 ? 1 : per_sm));
+        kern<<<grid, 8 * 32, smem, s>>>(tv, plan->d_heavy, plan->n_heavy, plan->d_light, plan->n_light,
+                                        xo.gallop_ratio, counters, acc, status, nullptr);
+    }
+    k_noalloc_finalize<<<1, 1, 0, s>>>(acc, (int)pattern, res, status);
+    EH_CUDA_TRY(cudaGetLastError());
+    unsigned long long r = 0;
+    uint32_t st = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&r, res, 8, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st & DEV_ST_TIMEOUT) { eh_set_error("eh_count_noalloc: a bounded device wait timed out"); return EH_ETIMEOUT; }
+    if (st & DEV_ST_OVERFLOW) { eh_set_error("eh_count_noalloc: count exceeds uint64"); return EH_EOVERFLOW; }
+    if (st) { eh_set_error("eh_count_noalloc: device status 0x%x", st); return EH_ECUDA; }
+    *out_count = r;
+    return EH_OK;
+}

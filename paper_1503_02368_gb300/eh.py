@@ -56,7 +56,7 @@ class ServerStats(ctypes.Structure):
                 ("mean_batch", ctypes.c_double)]
 
 
-EXPORTED = ["eh_build_trie", "eh_count", "eh_count_ex", "eh_count_async", "eh_count_status", "eh_count_info_get",
+EXPORTED = ["eh_build_trie", "eh_count", "eh_count_ex", "eh_count_noalloc", "eh_count_async", "eh_count_status", "eh_count_info_get",
             "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_trie_stats_get", "eh_trie_export",
             "eh_free_trie", "eh_last_error", "eh_server_create", "eh_server_submit", "eh_server_poll",
             "eh_server_wait", "eh_server_latency", "eh_server_stats_get", "eh_server_destroy"]
@@ -85,6 +85,8 @@ def lib():
     L.eh_count.argtypes = [vp, st, u32p, u32, vp, u64p]
     L.eh_count_ex.restype = st
     L.eh_count_ex.argtypes = [vp, st, u32p, u32, ctypes.POINTER(ExecOpts), vp, u64p]
+    L.eh_count_noalloc.restype = st
+    L.eh_count_noalloc.argtypes = [vp, st, vp, u64p]
     L.eh_count_async.restype = st
     L.eh_count_async.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, vp]
     L.eh_count_status.restype = st

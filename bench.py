@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="triangle", choices=["triangle", "batch", "serve", "all"],
+                    help="triangle: the headline line; batch/serve/all add the query-batch and serving results")
+    ap.add_argument("--serve-queries", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -162,6 +165,115 @@ def cpu_baseline(g, seconds, seed=7):
     return {"value": done_edges / t_total, "unit": "edges/s", "cores": cores, "kind": "oracle",
             "sample": "outer-loop vertices %d of %d (random order, seed %d), %d pruned edges, %.1f s; "
                       "oracle adjacency build excluded" % (pos, g["n"], seed, done_edges, t_total)}
+
+
+def bench_batch(eh, tau=32, reps=3, log=None):
+    """4,096 triangle/4-clique queries on R-MAT-20 ego nets: one persistent batch
+    vs one query at a time (same kernels); counts must agree exactly."""
+    import numpy as np
+    import torch
+    from synth import workloads as W
+    from paper_1503_02368_gb300 import autotune
+    g = W.rmat20_ego_batch()
+    pats = ["clique4" if p else "triangle" for p in g["patterns"]]
+    best = autotune.load("rmat_s20_ego4096")
+    if best:
+        tau = best["tau"]
+    xo = eh.exec_opts(cta_warps=best["cta_warps"], light_max=best["light_max"]) if best else None
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+    c0, s0 = trie.count_batch(pats, g["offsets"], g["pool"], mode=0, xopts=xo)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        c, st = trie.count_batch(pats, g["offsets"], g["pool"], mode=0, xopts=xo)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    c1, s1 = trie.count_batch(pats, g["offsets"], g["pool"], mode=1, xopts=xo)
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json"))).get("rmat_s20_ego4096")
+    exact = None
+    if gold:
+        exact = all(int(c0[int(q)]) == v["count"] for q, v in gold["queries"].items())
+    ok = bool(np.array_equal(c0, c) and np.array_equal(c0, c1) and not s0.any() and not s1.any())
+    trie.close()
+    nq = len(pats)
+    return {"workload": "rmat_s20_ef16 + 4096 ego nets |S| log-uniform 64..65536, triangle/4-clique alternating",
+            "queries": nq, "subset_ids": int(len(g["pool"])), "tau": tau,
+            "exec": {"cta_warps": best["cta_warps"], "light_max": best["light_max"]} if best else "defaults",
+            "batched_qps": nq / min(ts), "batched_s": min(ts), "one_launch_per_query_qps": nq / t_one,
+            "one_launch_per_query_s": t_one, "speedup": t_one / min(ts), "same_counts": ok,
+            "exact_vs_oracle_sample": exact,
+            "timing": "host wall clock around eh_count_batch (host subsets in, counts out), best of %d" % reps}
+
+
+def bench_serve(eh, n_queries=1500, tau=32, log=None):
+    """Resident R-MAT-24; ego-net queries (induced edges log-uniform 100..1e6),
+    patterns uniform over triangle / 4-clique / lollipop; closed-loop saturation,
+    then Poisson arrivals at 0.5x, 0.8x, 1.0x of it; p50/p99 latency."""
+    import threading
+    import numpy as np
+    import torch
+    from synth import workloads as W
+    g = W.rmat24_serve(n_queries=n_queries)
+    names = ("triangle", "clique4", "lollipop")
+    pats = [names[p] for p in g["patterns"]]
+    subsets = [g["pool"][g["offsets"][q]:g["offsets"][q + 1]] for q in range(n_queries)]
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+    budget = 48 << 30
+    res = {"workload": "rmat_s24_ef16 resident; ego nets with induced edges log-uniform 100..1e6; "
+                       "triangle/4-clique/lollipop uniform", "queries": n_queries,
+           "budget_bytes": budget, "max_batch": 64, "max_inflight": 4, "tau": tau}
+
+    def run(arrivals):
+        srv = eh.Server(trie, budget, max_batch=64, max_inflight=4)
+        tk = [None] * len(arrivals)
+        sub_t = [0.0] * len(arrivals)
+        t_start = time.perf_counter()
+        for q, at in enumerate(arrivals):
+            now = time.perf_counter() - t_start
+            if at > now:
+                time.sleep(at - now)
+            while True:
+                t = srv.submit(pats[q], subsets[q])
+                if t is not None:
+                    break
+                time.sleep(0.0005)
+            tk[q] = t
+            sub_t[q] = time.perf_counter() - t_start
+        out = [srv.wait(t, timeout_ms=600000) for t in tk]
+        t_end = time.perf_counter() - t_start
+        lat = [sub_t[q] - arrivals[q] + srv.latency(tk[q]) for q in range(len(arrivals))]
+        st = srv.stats()
+        srv.close()
+        return out, lat, t_end, st
+
+    out, lat, span, st = run([0.0] * n_queries)          # saturation (closed loop)
+    sat = n_queries / span
+    res["saturation_qps"] = sat
+    res["saturation_mean_batch"] = st["mean_batch"]
+    counts = [c for c, _ in out]
+    ok_status = all(s_ == 0 for _, s_ in out)
+    # each result equals the query alone
+    rng = np.random.default_rng(0)
+    sample = rng.choice(n_queries, size=min(64, n_queries), replace=False)
+    alone_ok = all(trie.count(pats[q], subset=subsets[q]) == counts[q] for q in sample)
+    res["same_alone_and_in_mix"] = bool(alone_ok and ok_status)
+    res["open_loop"] = []
+    for frac in (0.5, 0.8, 1.0):
+        lam = frac * sat
+        gaps = rng.exponential(1.0 / lam, size=n_queries)
+        arr = np.cumsum(gaps) - gaps[0]
+        out2, lat2, span2, st2 = run(list(arr))
+        same = [c for c, _ in out2] == counts
+        res["open_loop"].append({"rate_qps": lam, "achieved_qps": n_queries / span2,
+                                 "p50_ms": 1e3 * float(np.percentile(lat2, 50)),
+                                 "p99_ms": 1e3 * float(np.percentile(lat2, 99)),
+                                 "mean_batch": st2["mean_batch"], "same_counts": same})
+    trie.close()
+    return res
 
 
 def run_reference(args):
@@ -297,6 +409,12 @@ def run_eh(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, args.cpu_seconds)
 
+    extra = {}
+    if rank == 0 and args.workload in ("batch", "all"):
+        extra["batch"] = bench_batch(eh, args.tau)
+    if rank == 0 and args.workload in ("serve", "all"):
+        extra["serve"] = bench_serve(eh, args.serve_queries, args.tau)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -308,6 +426,7 @@ def run_eh(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps,
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)}}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     trie.close()
     if world > 1:

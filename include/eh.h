@@ -198,6 +198,21 @@ eh_status eh_count_batch_ex(const eh_trie *trie, const eh_query *queries, uint32
                             const uint32_t *subset_pool, uint64_t pool_len, const eh_exec_opts *xopts,
                             uint32_t mode, void *stream, uint64_t *out_counts, eh_status *out_status);
 
+/* Where the calling thread's last eh_count_batch / eh_count_batch_ex spent
+ * its time, summed over its device batches: prepare = subsets to device,
+ * sort, membership bitmaps, induced sub-tries, layouts, work lists (host wall
+ * clock, stream synchronised); count = the persistent count launch and the
+ * result copy. */
+typedef struct {
+    uint64_t queries, batches;
+    uint64_t sub_vertices;      /* distinct (query, vertex) pairs */
+    uint64_t sub_set_elements;  /* padded elements of the induced pruned sets */
+    uint64_t heavy_items, light_items;
+    double prepare_s, count_s;
+} eh_batch_profile;
+
+eh_status eh_batch_profile_get(eh_batch_profile *out);
+
 eh_status eh_trie_stats_get(const eh_trie *trie, eh_trie_stats *out);
 
 /* eh_trie_export -- copies the trie to host arrays for inspection (tests).
@@ -212,6 +227,14 @@ eh_status eh_trie_export(const eh_trie *trie, uint32_t which, uint32_t *new_to_o
                          uint64_t *bits_off, uint32_t *out_words);
 
 void eh_free_trie(eh_trie *trie);
+
+/* eh_selftest_wait_timeout -- runs one kernel that waits, with the bounded
+ * wait every count kernel uses for its bulk copies, on a barrier phase that
+ * nothing completes.  The wait gives up after limit_us microseconds and the
+ * kernel reports it through its status word: the call returns EH_ETIMEOUT
+ * (the expected result) and the CUDA context stays usable.  For tests of
+ * the failure path; no GPU fault is involved. */
+eh_status eh_selftest_wait_timeout(uint32_t limit_us, void *stream);
 
 const char *eh_last_error(void);
 

@@ -15,13 +15,21 @@
 //      N+(v), with warp ballot/scan compaction of the survivors;
 //   4. degrees in the induced graph (for the lollipop), set-level layouts;
 //   5. a work list over the sub-vertices of all queries, heaviest first;
-//   6. one launch of the fused batch kernel.
+//   6. one launch of the fused batch kernel, captured in a CUDA graph with the
+//      clears of its counters and launched as that graph.
 #include "eh_internal.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <vector>
 
 namespace {
+
+thread_local eh_batch_profile g_prof;
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 constexpr uint32_t FULLM = 0xffffffffu;
 
@@ -278,6 +286,7 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
                     eh_status *out_status) {
     const uint32_t nq = (uint32_t)sel.size();
     if (nq == 0) return EH_OK;
+    const double t_begin = now_s();
     Scratch sc(s);
     const uint32_t n = t->n;
     // host tables
@@ -406,22 +415,57 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     }
 
     // 6. one persistent launch for the whole batch
+    const double t_prepared = now_s();   // the stream is idle here (synchronised above)
     unsigned long long *d_out = nullptr, *d_cnt = nullptr;
     uint32_t *d_bst = nullptr;   // this batch's device status word
     EH_TRY(sc.alloc(&d_out, 2ull * nq));
     EH_TRY(sc.alloc(&d_cnt, 2));
     EH_TRY(sc.alloc(&d_bst, 1));
-    EH_CUDA_TRY(cudaMemsetAsync(d_out, 0, 16ull * nq, s));
-    EH_CUDA_TRY(cudaMemsetAsync(d_bst, 0, 4, s));
-    EH_TRY(eh_launch_batch(bv, heavy, n_heavy, light, n_light, xo, s, d_out, d_cnt, d_bst, arena, per_warp,
-                           nullptr));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));   // every buffer above is ready
+    // The count phase (clears + the one persistent launch) is captured in a
+    // CUDA graph on this thread's capture stream and launched as a graph.
+    static thread_local cudaStream_t cs = nullptr;
+    if (!cs) EH_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    EH_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    eh_status lst = EH_OK;
+    if (cudaMemsetAsync(d_out, 0, 16ull * nq, cs) != cudaSuccess || cudaMemsetAsync(d_bst, 0, 4, cs) != cudaSuccess)
+        lst = EH_ECUDA;
+    if (lst == EH_OK)
+        lst = eh_launch_batch(bv, heavy, n_heavy, light, n_light, xo, cs, d_out, d_cnt, d_bst, arena, per_warp,
+                              nullptr);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (lst != EH_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (lst == EH_OK) eh_set_error("batch graph capture: %s", cudaGetErrorString(ce));
+        return lst != EH_OK ? lst : EH_ECUDA;
+    }
+    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(gexec, cs);
     std::vector<unsigned long long> h_out(2ull * nq);
     std::vector<uint32_t> h_stat(nq);
     uint32_t bst = 0;
-    EH_CUDA_TRY(cudaMemcpyAsync(h_out.data(), d_out, 16ull * nq, cudaMemcpyDeviceToHost, s));
-    EH_CUDA_TRY(cudaMemcpyAsync(h_stat.data(), d_qstat, 4ull * nq, cudaMemcpyDeviceToHost, s));
-    EH_CUDA_TRY(cudaMemcpyAsync(&bst, d_bst, 4, cudaMemcpyDeviceToHost, s));
-    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_out.data(), d_out, 16ull * nq, cudaMemcpyDeviceToHost, cs);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_stat.data(), d_qstat, 4ull * nq, cudaMemcpyDeviceToHost, cs);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&bst, d_bst, 4, cudaMemcpyDeviceToHost, cs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        eh_set_error("batch count graph: %s", cudaGetErrorString(ce));
+        return EH_ECUDA;
+    }
+    const double t_done = now_s();
+    g_prof.queries += nq;
+    g_prof.sub_vertices += V;
+    g_prof.sub_set_elements += total;
+    g_prof.heavy_items += n_heavy;
+    g_prof.light_items += n_light;
+    g_prof.prepare_s += t_prepared - t_begin;
+    g_prof.count_s += t_done - t_prepared;
+    g_prof.batches += 1;
     eh_status dst = EH_OK;
     if (bst & DEV_ST_TIMEOUT) { dst = EH_ETIMEOUT; eh_set_error("a bounded device wait timed out"); }
     else if (bst) { dst = EH_ECUDA; eh_set_error("batch kernel reported status 0x%x", bst); }
@@ -459,6 +503,7 @@ extern "C" eh_status eh_count_batch_ex(const eh_trie *trie, const eh_query *quer
     eh_trie *t = const_cast<eh_trie *>(trie);
     cudaStream_t s = (cudaStream_t)stream;
     const eh_exec_opts xo = eh_exec_defaults(xopts);
+    memset(&g_prof, 0, sizeof(g_prof));
     std::vector<uint32_t> subset_q, whole_q;
     eh_status first = EH_OK;
     for (uint32_t i = 0; i < n_queries; ++i) {
@@ -520,4 +565,10 @@ eh_status eh_count_subset(const eh_trie *trie, eh_pattern pattern, const uint32_
     eh_status st = EH_OK;
     eh_status r = eh_count_batch_ex(trie, &q, 1, subset, subset_len, xopts, 0, stream, out_count, &st);
     return r != EH_OK ? r : st;
+}
+
+extern "C" eh_status eh_batch_profile_get(eh_batch_profile *out) {
+    if (!out) { eh_set_error("eh_batch_profile_get: NULL argument"); return EH_EINVAL; }
+    *out = g_prof;
+    return EH_OK;
 }

@@ -25,7 +25,8 @@ namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr uint32_t BM_CAP_WORDS = 8192;        // 32 KB on-chip bitmap: value ranges up to 262,144
-constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 22; // bounded wait for a bulk copy
+constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;          // bounded wait for a bulk copy: iterations
+constexpr uint64_t MBAR_TIME_LIMIT_NS = 2000000000ull;  // ... and wall time (2 s)
 
 enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2 };
 
@@ -62,15 +63,25 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// returns true when the phase with the given parity completed within the limit
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true when the phase with the given parity completed within the limits
+// (an iteration count and a wall-time bound, whichever comes first)
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity,
+                                          uint64_t limit_ns = MBAR_TIME_LIMIT_NS) {
     uint32_t done = 0;
+    const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < MBAR_SPIN_LIMIT && !done; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(smem_u32(mbar)), "r"(parity)
             : "memory");
+        if (!done && (it & 63) == 63 && global_ns() - t0 > limit_ns) break;
     }
     return done != 0;
 }
@@ -123,14 +134,16 @@ __device__ __forceinline__ void pair_bitmap(const TrieView &tv, const uint32_t *
             return;
         }
     }
-    // uint B: each element probes A's bitmap (padding EH_PAD is out of range)
+    // uint B: each element probes A's bitmap (padding EH_PAD is out of range);
+    // two 128-bit loads in flight per lane
     const uint32_t *bp = tv.nbr + dv.off;
     const uint32_t base = a_lo * 32, nbits = a_nw * 32;
-    for (uint32_t p = lane * 4; p < dv.len; p += 128) {
-        uint4 e = ldg4(bp + p);
-        uint32_t w[4] = {e.x, e.y, e.z, e.w};
+    for (uint32_t p = lane * 4; p < dv.len; p += 256) {
+        uint4 e0 = ldg4(bp + p);
+        uint4 e1 = p + 128 < dv.len ? ldg4(bp + p + 128) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+        uint32_t w[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 8; ++c) {
             uint32_t x = w[c] - base;
             if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) on_match<MODE>(acc, w[c], duv, tv, vt);
         }
@@ -144,6 +157,25 @@ __device__ __forceinline__ uint32_t lower_bound(const uint32_t *A, uint32_t lo, 
         if (A[mid] < key) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// Descriptor of lane `src` broadcast to the warp (descriptors of upcoming
+// pairs are loaded one per lane, in parallel, then handed out pair by pair).
+__device__ __forceinline__ SetDesc bcast_desc(const SetDesc &d, int src) {
+    SetDesc r;
+    r.off = __shfl_sync(FULL, d.off, src);
+    r.len = __shfl_sync(FULL, d.len, src);
+    r.deg = __shfl_sync(FULL, d.deg, src);
+    r.woff = __shfl_sync(FULL, d.woff, src);
+    r.lo_word = __shfl_sync(FULL, d.lo_word, src);
+    r.nwords = __shfl_sync(FULL, d.nwords, src);
+    return r;
+}
+
+__device__ __forceinline__ SetDesc empty_desc() {
+    SetDesc d;
+    d.off = 0; d.len = 0; d.deg = 0; d.woff = 0; d.lo_word = 0; d.nwords = 0;
+    return d;
 }
 
 // A sorted array (shared or global), effective prefix A[0..j) ∩ B
@@ -246,9 +278,10 @@ __device__ void light_vertex(const TrieView &tv, uint32_t u, uint32_t ratio, Acc
     const SetDesc du = tv.desc[u];
     const uint32_t k = du.len;
     const uint32_t a = lane < k ? __ldg(&tv.nbr[du.off + lane]) : EH_PAD;
+    const SetDesc mine = (lane >= 1 && lane < k) ? tv.desc[a] : empty_desc();
     for (uint32_t j = 1; j < k; ++j) {
         const uint32_t v = __shfl_sync(FULL, a, j);
-        const SetDesc dv = tv.desc[v];
+        const SetDesc dv = bcast_desc(mine, j);
         if (dv.len == 0) continue;
         const bool hit = light_match(tv, a, j, dv, ratio);
         if (hit) on_match<MODE>(acc, a, du.deg + dv.deg, tv, vt);
@@ -334,9 +367,11 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
     return true;
 }
 
+constexpr uint32_t PAIR_BATCH = 8;   // pairs a warp takes at a time from its CTA's vertex
+
 __device__ __forceinline__ uint32_t next_j(uint32_t *s_next) {
     uint32_t j = 0;
-    if ((threadIdx.x & 31) == 0) j = atomicAdd(s_next, 1u);
+    if ((threadIdx.x & 31) == 0) j = atomicAdd(s_next, PAIR_BATCH);
     return __shfl_sync(FULL, j, 0);
 }
 
@@ -350,21 +385,33 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
     StagedA st;
     if (!stage_set<WARPS>(tv, du, sA, mbar, phase, st, status)) return false;
     for (;;) {
-        const uint32_t j = next_j(s_next);
-        if (j >= st.len) break;
-        const uint32_t v = st.amode == 0 ? __ldg(&st.Ag[j]) : st.A[j];
-        const SetDesc dv = tv.desc[v];
-        if (dv.len == 0) continue;
-        const uint32_t duv = du.deg + dv.deg;
-        unsigned long long t0 = acc.t;
-        if (st.amode == 0) pair_bitmap<MODE>(tv, sA, st.a_lo, st.a_nw, dv, duv, acc, vt);
-        else pair_sorted<MODE>(tv, st.A, j, dv, duv, ratio, acc, vt);
-        if (MODE == M_VERTEX) {
-            unsigned long long pc = acc.t - t0;
-            for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
-            if (lane == 0 && pc) {
-                atomicAdd(&vt[u], pc);
-                atomicAdd(&vt[v], pc);
+        const uint32_t j0 = next_j(s_next);
+        if (j0 >= st.len) break;
+        // the next PAIR_BATCH pairs: v and its descriptor loaded one per lane
+        const uint32_t jl = j0 + lane;
+        uint32_t vl = 0;
+        SetDesc mine = empty_desc();
+        if (lane < PAIR_BATCH && jl < st.len) {
+            vl = st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl];
+            mine = tv.desc[vl];
+        }
+        const uint32_t nb = min(PAIR_BATCH, st.len - j0);
+        for (uint32_t i = 0; i < nb; ++i) {
+            const uint32_t j = j0 + i;
+            const uint32_t v = __shfl_sync(FULL, vl, i);
+            const SetDesc dv = bcast_desc(mine, i);
+            if (dv.len == 0) continue;
+            const uint32_t duv = du.deg + dv.deg;
+            unsigned long long t0 = acc.t;
+            if (st.amode == 0) pair_bitmap<MODE>(tv, sA, st.a_lo, st.a_nw, dv, duv, acc, vt);
+            else pair_sorted<MODE>(tv, st.A, j, dv, duv, ratio, acc, vt);
+            if (MODE == M_VERTEX) {
+                unsigned long long pc = acc.t - t0;
+                for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
+                if (lane == 0 && pc) {
+                    atomicAdd(&vt[u], pc);
+                    atomicAdd(&vt[v], pc);
+                }
             }
         }
     }
@@ -570,15 +617,84 @@ __device__ uint32_t emit_sorted(const TrieView &tv, const uint32_t *A, uint32_t 
     return ns;
 }
 
-// level 2 over a materialised sorted S
+// Level 2 over a materialised sorted S: K4 += sum_{z in S} |S_<z ∩ N+(z)|
+// (= the edges of G[S]; N+(z) ⊂ [0, z) keeps S's elements >= z out).
+//
+// When S is dense (its value range needs at most one 32-bit word per element
+// and fits the warp's bitmap buffer) it also gets a bitmap, and the warp
+// takes 32 z's at a time, one per lane: a lane whose N+(z) is a bitset ANDs
+// it with S's bitmap over their overlapping words (128 bits per step), a lane
+// whose N+(z) is a short uint array probes S's bitmap with each element.  The
+// remaining z's (and every z of a sparse S) run the warp-wide routines, z by
+// z, with their descriptors loaded one per lane beforehand.
+constexpr uint32_t SB_CAP_WORDS = 256;    // per-warp bitmap of S: value ranges up to 8,192
+constexpr uint32_t LANE_UINT_MAX = 64;    // a lane walks a uint N+(z) alone up to this length
+
 __device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t *S, uint32_t ns, uint32_t ratio,
-                                              Acc &acc) {
-    for (uint32_t i = 1; i < ns; ++i) {
-        const uint32_t z = S[i];
-        const SetDesc dz = tv.desc[z];
-        if (dz.len == 0) continue;
-        pair_sorted<M_COUNT>(tv, S, i, dz, 0, ratio, acc, nullptr);
+                                              uint32_t *Sbm, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    uint32_t s_lo = 0, s_nw = 0;
+    bool bm = false;
+    if (Sbm && ns >= 32) {
+        s_lo = (S[0] >> 7) << 2;
+        s_nw = (((S[ns - 1] >> 5) + 1 - s_lo) + 3) & ~3u;
+        bm = s_nw <= SB_CAP_WORDS && s_nw <= ns;
+        if (bm) {
+            for (uint32_t w = lane; w < s_nw; w += 32) Sbm[w] = 0u;
+            __syncwarp();
+            for (uint32_t k = lane; k < ns; k += 32) {
+                const uint32_t e = S[k];
+                atomicOr(&Sbm[(e >> 5) - s_lo], 1u << (e & 31));
+            }
+            __syncwarp();
+        }
     }
+    for (uint32_t i0 = 1; i0 < ns; i0 += 32) {
+        const uint32_t il = i0 + lane;
+        const SetDesc mine = il < ns ? tv.desc[S[il]] : empty_desc();
+        const uint32_t cnt = min(32u, ns - i0);
+        uint32_t coop = __ballot_sync(FULL, il < ns && mine.len > 0);
+        if (bm) {
+            // lane-per-z over S's bitmap
+            bool mine_coop = false;
+            if (il < ns && mine.len > 0) {
+                uint32_t c = 0;
+                if (mine.nwords) {
+                    const uint32_t lo = max(s_lo, mine.lo_word), hi = min(s_lo + s_nw, mine.lo_word + mine.nwords);
+                    const uint32_t *zw = tv.words + mine.woff - mine.lo_word;
+                    for (uint32_t w = lo; w < hi; w += 4) {
+                        const uint4 b = ldg4(zw + w);
+                        const uint4 a = *reinterpret_cast<const uint4 *>(Sbm + (w - s_lo));
+                        c += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+                    }
+                } else if (mine.len <= LANE_UINT_MAX) {
+                    const uint32_t *zp = tv.nbr + mine.off;
+                    const uint32_t base = s_lo * 32, nbits = s_nw * 32;
+                    for (uint32_t p = 0; p < mine.len; p += 4) {
+                        const uint4 e = ldg4(zp + p);
+                        const uint32_t w4[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t x = w4[q] - base;
+                            if (x < nbits) c += (Sbm[x >> 5] >> (x & 31)) & 1u;
+                        }
+                    }
+                } else {
+                    mine_coop = true;
+                }
+                acc.t += c;
+            }
+            coop = __ballot_sync(FULL, mine_coop);
+        }
+        while (coop) {
+            const uint32_t k = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const SetDesc dz = bcast_desc(mine, k);
+            pair_sorted<M_COUNT>(tv, S, i0 + k, dz, 0, ratio, acc, nullptr);
+        }
+        (void)cnt;
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
@@ -588,7 +704,7 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
 
 template <int WARPS>
 __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_t ratio, uint32_t *sA, uint32_t *sS,
-                                         uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
+                                         uint32_t *sB, uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
                                          uint32_t *status, uint32_t *arena, uint64_t arena_per_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
@@ -597,10 +713,15 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
     StagedA st;
     if (!stage_set<WARPS>(tv, dx, sA, mbar, phase, st, status)) return false;
     for (;;) {
-        const uint32_t j = next_j(s_next);
-        if (j >= st.len) break;
-        const uint32_t y = st.amode == 0 ? __ldg(&st.Ag[j]) : st.A[j];
-        const SetDesc dy = tv.desc[y];
+        const uint32_t j0 = next_j(s_next);
+        if (j0 >= st.len) break;
+        const uint32_t jl = j0 + lane;
+        SetDesc mine = empty_desc();
+        if (lane < PAIR_BATCH && jl < st.len) mine = tv.desc[st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl]];
+        const uint32_t nbat = min(PAIR_BATCH, st.len - j0);
+        for (uint32_t i = 0; i < nbat; ++i) {
+        const uint32_t j = j0 + i;
+        const SetDesc dy = bcast_desc(mine, i);
         if (dy.len < 2) continue;
         const uint32_t bound = min(j, dy.len);
         uint32_t *S = bound <= S_CAP ? sS + warp * S_CAP : arena + gwarp * arena_per_warp;
@@ -610,8 +731,9 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
         }
         uint32_t ns = st.amode == 0 ? emit_bitmap(tv, sA, st.a_lo, st.a_nw, dy, S)
                                     : emit_sorted(tv, st.A, j, dy, ratio, S);
-        clique_level2(tv, S, ns, ratio, acc);
+        clique_level2(tv, S, ns, ratio, sB + warp * SB_CAP_WORDS, acc);
         __syncwarp();
+        }
     }
     __syncthreads();
     return true;
@@ -623,20 +745,35 @@ __device__ void k4_light(const TrieView &tv, uint32_t x, uint32_t ratio, Acc &ac
     const SetDesc dx = tv.desc[x];
     const uint32_t k = dx.len;
     const uint32_t a = lane < k ? __ldg(&tv.nbr[dx.off + lane]) : EH_PAD;
+    const SetDesc mine = lane < k ? tv.desc[a] : empty_desc();
     for (uint32_t j = 2; j < k; ++j) {
-        const uint32_t y = __shfl_sync(FULL, a, j);
-        const SetDesc dy = tv.desc[y];
+        const SetDesc dy = bcast_desc(mine, j);
         if (dy.len < 2) continue;
         const uint32_t m = __ballot_sync(FULL, light_match(tv, a, j, dy, ratio));
         const uint32_t ns = __popc(m);
         if (ns < 2) continue;
+        // S = the matching lanes' elements (and descriptors), compacted in order
         const uint32_t src = (uint32_t)lane < ns ? nth_set_bit(m, lane) : 0u;
         uint32_t sv = __shfl_sync(FULL, a, src);
+        const SetDesc sd = bcast_desc(mine, src);
         if ((uint32_t)lane >= ns) sv = EH_PAD;
-        for (uint32_t i = 1; i < ns; ++i) {
-            const uint32_t z = __shfl_sync(FULL, sv, i);
-            const SetDesc dz = tv.desc[z];
-            if (dz.len == 0) continue;
+        // lane i (z = S[i]) with a bitset N+(z) probes S[0..i) itself, reading
+        // S's elements from the lower lanes; the other z's run warp-wide
+        const bool lane_bits = (uint32_t)lane >= 1 && (uint32_t)lane < ns && sd.len > 0 && sd.nwords;
+        uint32_t c = 0;
+        const uint32_t zbase = sd.lo_word * 32, znbits = sd.nwords * 32;
+        for (uint32_t t2 = 0; t2 + 1 < ns; ++t2) {
+            const uint32_t e = __shfl_sync(FULL, sv, t2);
+            const uint32_t x = e - zbase;
+            if (lane_bits && t2 < (uint32_t)lane && x < znbits)
+                c += (__ldg(&tv.words[sd.woff + (x >> 5)]) >> (x & 31)) & 1u;
+        }
+        acc.t += c;
+        uint32_t coop = __ballot_sync(FULL, (uint32_t)lane >= 1 && (uint32_t)lane < ns && sd.len > 0 && !sd.nwords);
+        while (coop) {
+            const uint32_t i = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const SetDesc dz = bcast_desc(sd, i);
             if (light_match(tv, sv, i, dz, ratio)) acc.t += 1;
         }
     }
@@ -651,6 +788,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sA = smem;
     uint32_t *sS = smem + BM_CAP_WORDS;
+    uint32_t *sB = sS + WARPS * S_CAP;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_item, s_next;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -663,7 +801,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
-        if (!k4_heavy<WARPS>(tv, heavy[item], ratio, sA, sS, &mbar, phase, &s_next, acc, status, arena,
+        if (!k4_heavy<WARPS>(tv, heavy[item], ratio, sA, sS, sB, &mbar, phase, &s_next, acc, status, arena,
                              arena_per_warp))
             return;
     }
@@ -709,6 +847,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch(BatchView bv, const uint32
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sA = smem;
     uint32_t *sS = smem + BM_CAP_WORDS;
+    uint32_t *sB = sS + WARPS * S_CAP;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_item, s_next;
     __shared__ unsigned long long red_t[WARPS], red_s[WARPS];
@@ -729,7 +868,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch(BatchView bv, const uint32
         Acc acc{0, 0};
         bool ok;
         if (pat == EH_CLIQUE4)
-            ok = k4_heavy<WARPS>(tv, u, ratio, sA, sS, &mbar, phase, &s_next, acc, status, arena, arena_per_warp);
+            ok = k4_heavy<WARPS>(tv, u, ratio, sA, sS, sB, &mbar, phase, &s_next, acc, status, arena, arena_per_warp);
         else if (pat == EH_TRIANGLE)
             ok = tri_heavy<M_COUNT, WARPS>(tv, u, ratio, sA, &mbar, phase, &s_next, acc, status, nullptr);
         else
@@ -784,7 +923,7 @@ eh_status launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n_he
                        unsigned long long *d_counters, uint32_t *d_status, uint32_t *arena, uint64_t per_warp,
                        uint32_t *grid_warps) {
     auto kern = k_batch<WARPS>;
-    const int smem = (BM_CAP_WORDS + WARPS * S_CAP) * 4;
+    const int smem = (BM_CAP_WORDS + WARPS * (S_CAP + SB_CAP_WORDS)) * 4;
     EH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
@@ -802,7 +941,7 @@ template <int WARPS>
 eh_status launch_k4(eh_trie *t, const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
                     unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status) {
     auto kern = k_clique4<WARPS>;
-    const int smem = (BM_CAP_WORDS + WARPS * S_CAP) * 4;
+    const int smem = (BM_CAP_WORDS + WARPS * (S_CAP + SB_CAP_WORDS)) * 4;
     EH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
@@ -991,7 +1130,7 @@ extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, v
     const TrieView tv = t->view();
 
     auto kern4 = k_clique4<8>;
-    const int smem4 = (BM_CAP_WORDS + 8 * S_CAP) * 4;
+    const int smem4 = (BM_CAP_WORDS + 8 * (S_CAP + SB_CAP_WORDS)) * 4;
     unsigned grid4 = 0;
     uint64_t per_warp = 0;
     if (pattern == EH_CLIQUE4) {
@@ -1037,5 +1176,39 @@ extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, v
     if (st & DEV_ST_OVERFLOW) { eh_set_error("eh_count_noalloc: count exceeds uint64"); return EH_EOVERFLOW; }
     if (st) { eh_set_error("eh_count_noalloc: device status 0x%x", st); return EH_ECUDA; }
     *out_count = r;
+    return EH_OK;
+}
+
+// ------------------------------------------------------ bounded-wait self-test
+//
+// A kernel that waits, with the count kernels' bounded wait, on an mbarrier
+// phase that nothing completes: the wait gives up after `limit_us`, the
+// kernel records DEV_ST_TIMEOUT and returns, and the context stays usable.
+
+namespace {
+__global__ void k_selftest_wait(uint32_t *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    const bool ok = mbar_wait(&mbar, 0, limit_ns);   // no arrival, no copy: never completes
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, DEV_ST_TIMEOUT);
+}
+}  // namespace
+
+extern "C" eh_status eh_selftest_wait_timeout(uint32_t limit_us, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *d = nullptr;
+    EH_TRY(dev_alloc(&d, 1, s));
+    uint32_t h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, 4, s);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 64, 0, s>>>(d, (uint64_t)limit_us * 1000ull);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, s);
+    dev_free(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { eh_set_error("self-test: %s", cudaGetErrorString(e)); return EH_ECUDA; }
+    if (h & DEV_ST_TIMEOUT) { eh_set_error("self-test: the bounded wait gave up as designed"); return EH_ETIMEOUT; }
     return EH_OK;
 }

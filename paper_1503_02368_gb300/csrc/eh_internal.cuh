@@ -11,7 +11,7 @@
 #include <vector>
 #include <map>
 
-#include "../../include/eh.h"
+#include "eh.h"
 
 // ------------------------------------------------------------------ errors
 

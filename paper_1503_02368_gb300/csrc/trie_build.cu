@@ -46,13 +46,20 @@ __global__ void k_unique_scatter(const uint64_t *__restrict__ keys, const uint32
     if (flags[i]) out[pos[i]] = keys[i];
 }
 
+// degrees of both endpoints; lanes hitting the same vertex (hubs) add once
+// per warp, so high-degree counters do not serialise on atomics
 __global__ void k_degrees(const uint64_t *__restrict__ ukeys, uint64_t m, int nb, uint32_t *deg) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    uint64_t k = ukeys[i];
-    uint32_t lo = (uint32_t)(k >> nb), hi = (uint32_t)(k & ((1ull << nb) - 1));
-    atomicAdd(&deg[lo], 1u);
-    atomicAdd(&deg[hi], 1u);
+    const bool valid = i < m;
+    uint64_t k = valid ? ukeys[i] : 0ull;
+    uint32_t ends[2] = {valid ? (uint32_t)(k >> nb) : 0xFFFFFFFFu,
+                        valid ? (uint32_t)(k & ((1ull << nb) - 1)) : 0xFFFFFFFFu};
+    const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        uint32_t peers = __match_any_sync(0xffffffffu, ends[e]);
+        if (valid && (peers & lt) == 0) atomicAdd(&deg[ends[e]], (uint32_t)__popc(peers));
+    }
 }
 
 __global__ void k_max_u32(const uint32_t *__restrict__ x, uint64_t n, uint32_t *out) {

@@ -50,6 +50,12 @@ class Query(ctypes.Structure):
     _fields_ = [("pattern", ctypes.c_uint32), ("subset_len", ctypes.c_uint32), ("subset_off", ctypes.c_uint64)]
 
 
+class BatchProfile(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("sub_vertices", ctypes.c_uint64),
+                ("sub_set_elements", ctypes.c_uint64), ("heavy_items", ctypes.c_uint64),
+                ("light_items", ctypes.c_uint64), ("prepare_s", ctypes.c_double), ("count_s", ctypes.c_double)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
@@ -57,8 +63,8 @@ class ServerStats(ctypes.Structure):
 
 
 EXPORTED = ["eh_build_trie", "eh_count", "eh_count_ex", "eh_count_noalloc", "eh_count_async", "eh_count_status", "eh_count_info_get",
-            "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_trie_stats_get", "eh_trie_export",
-            "eh_free_trie", "eh_last_error", "eh_server_create", "eh_server_submit", "eh_server_poll",
+            "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_batch_profile_get", "eh_trie_stats_get", "eh_trie_export",
+            "eh_free_trie", "eh_last_error", "eh_selftest_wait_timeout", "eh_server_create", "eh_server_submit", "eh_server_poll",
             "eh_server_wait", "eh_server_latency", "eh_server_stats_get", "eh_server_destroy"]
 
 
@@ -100,10 +106,14 @@ def lib():
     L.eh_count_batch_ex.restype = st
     L.eh_count_batch_ex.argtypes = [vp, ctypes.POINTER(Query), u32, u32p, u64, ctypes.POINTER(ExecOpts), u32, vp,
                                     u64p, ctypes.POINTER(ctypes.c_int)]
+    L.eh_batch_profile_get.restype = st
+    L.eh_batch_profile_get.argtypes = [ctypes.POINTER(BatchProfile)]
     L.eh_trie_stats_get.restype = st
     L.eh_trie_stats_get.argtypes = [vp, ctypes.POINTER(TrieStats)]
     L.eh_trie_export.restype = st
     L.eh_trie_export.argtypes = [vp, u32, u32p, u64p, u32p, u32p, u32p, u32p, u64p, u32p]
+    L.eh_selftest_wait_timeout.restype = st
+    L.eh_selftest_wait_timeout.argtypes = [u32, vp]
     L.eh_free_trie.restype = None
     L.eh_free_trie.argtypes = [vp]
     L.eh_server_create.restype = st
@@ -150,6 +160,13 @@ def _stream(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def batch_profile():
+    """Phase times of this thread's last count_batch call."""
+    p = BatchProfile()
+    _check(lib().eh_batch_profile_get(ctypes.byref(p)))
+    return {f: getattr(p, f) for f, _ in BatchProfile._fields_}
 
 
 def build_opts(tau=32, min_bitset_len=0, flags=0):

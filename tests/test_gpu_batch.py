@@ -110,17 +110,18 @@ def test_batch_knobs_do_not_change_counts(eh, rmat12):
 
 
 def test_rmat20_ego4096_workload(eh):
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "workload_counts.json")))
+    gold = gold["rmat_s20_ego4096"]
     g = W.rmat20_ego_batch()
+    from tests.golden.make_golden import fingerprint
+    assert fingerprint(g) == gold["fingerprint"]
     off, pool, pq = g["offsets"], g["pool"], g["patterns"]
     pats = ["clique4" if p else "triangle" for p in pq]
     t = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
     c0, s0 = t.count_batch(pats, off, pool, mode=0)
     assert not s0.any()
-    o = oracle.Graph(g["n"], g["src"], g["dst"])
-    rng = np.random.default_rng(4)
-    sample = np.concatenate([np.arange(8), rng.choice(len(pats), 56, replace=False)])
-    sizes = np.diff(off)
-    sample = np.concatenate([sample, np.argsort(-sizes)[:4]])    # the largest subsets too
-    for q in sample:
-        want = o.induced(pool[off[q]:off[q + 1]]).count(pats[q], nthreads=8)
-        assert int(c0[q]) == want, (int(q), pats[q], int(sizes[q]))
+    for q, rec in gold["queries"].items():       # oracle counts of a sample, incl. the 4 largest
+        assert pats[int(q)] == rec["pattern"]
+        assert int(c0[int(q)]) == rec["count"], (q, rec)

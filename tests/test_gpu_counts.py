@@ -216,3 +216,15 @@ def test_chunglu_full_size(eh):
     assert t.stats()["n_edges"] == gold["m"]
     assert t.count("triangle") == gold["triangle"]
     assert t.count("clique4") == gold["clique4"]
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(eh):
+    # a wait on a barrier phase nothing completes gives up and reports, no fault
+    import time
+    t0 = time.time()
+    r = eh.lib().eh_selftest_wait_timeout(20000, None)      # 20 ms limit
+    assert r == 4                                            # EH_ETIMEOUT
+    assert time.time() - t0 < 10
+    g = W.er_10k_100k()
+    t = eh.Trie(g["src"], g["dst"], g["n"])
+    assert t.count("triangle") == GOLD["er_n10000_m100000"]["triangle"]

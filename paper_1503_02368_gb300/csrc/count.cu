@@ -367,7 +367,7 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
     return true;
 }
 
-constexpr uint32_t PAIR_BATCH = 8;   // pairs a warp takes at a time from its CTA's vertex
+constexpr uint32_t PAIR_BATCH = 4;   // pairs a warp takes at a time from its CTA's vertex
 
 __device__ __forceinline__ uint32_t next_j(uint32_t *s_next) {
     uint32_t j = 0;

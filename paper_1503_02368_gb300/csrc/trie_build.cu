@@ -389,7 +389,7 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     uint32_t act = 0, mo = 0;
     uint64_t nbs = 0, nne = 0;
     double sum = 0, sum2 = 0;
-    std::map<uint32_t, uint64_t> hist;
+    std::vector<uint64_t> hist((size_t)maxdeg + 1, 0);
     for (uint32_t v = 0; v < n; ++v) {
         if (hdeg[v]) ++act;
         mo = std::max(mo, hodeg[v]);
@@ -408,8 +408,8 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     double mean = n ? sum / n : 0, var = n ? sum2 / n - mean * mean : 0;
     uint32_t mode = 0;
     uint64_t best = 0;
-    for (auto &kv : hist)
-        if (kv.second > best) { best = kv.second; mode = kv.first; }
+    for (uint32_t d = 0; d <= maxdeg; ++d)
+        if (hist[d] > best) { best = hist[d]; mode = d; }
     t->density_skew = var > 0 ? 3.0 * (mean - mode) / std::sqrt(var) : 0.0;
     t->device_bytes = bytes;
     return EH_OK;

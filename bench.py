@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="eh", choices=["eh", "reference"])
-    ap.add_argument("--tau", type=int, default=32)
+    ap.add_argument("--tau", type=int, default=None,
+                    help="bitset threshold; default: the autotuned value for the workload (else 32)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -336,18 +337,25 @@ def run_eh(args):
     import paper_1503_02368_gb300 as eh
     from synth import workloads as W
 
+    from paper_1503_02368_gb300 import autotune
     g = W.rmat22()
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))["rmat_s22_ef16"]
-    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=args.tau)
+    tuned = autotune.load("rmat_s22_triangle")
+    tau = args.tau if args.tau is not None else (tuned["tau"] if tuned else 32)
+    warps = tuned["cta_warps"] if tuned and args.tau is None else 8
+    light_max = tuned["light_max"] if tuned and args.tau is None else 32
+    xo = eh.exec_opts(cta_warps=warps, light_max=light_max)
+    args.tau = tau
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
     st = trie.stats()
     m = st["n_edges"]
-    info = trie.info("triangle")
+    info = trie.info("triangle", xopts=xo)
     stream = torch.cuda.current_stream()
     out = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     for _ in range(args.warmup):
-        trie.count_async("triangle", out.data_ptr(), stream=stream)
+        trie.count_async("triangle", out.data_ptr(), xopts=xo, stream=stream)
     torch.cuda.synchronize()
     trie.status(stream)
     if world > 1:
@@ -361,7 +369,7 @@ def run_eh(args):
     for k in range(args.steps):
         flush.fill_(k)                      # L2 flush (256 MiB write) outside the timed interval
         evs[k][0].record(stream)
-        trie.count_async("triangle", out.data_ptr(), stream=stream)
+        trie.count_async("triangle", out.data_ptr(), xopts=xo, stream=stream)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -380,7 +388,7 @@ def run_eh(args):
     traffic = profile_traffic(os.path.join(ROOT, "paper_1503_02368_gb300", "csrc", "count.cu"))
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
-            "alg_bytes_per_launch": info["alg_bytes"], "kernel": "k_triangle<0,8>"}
+            "alg_bytes_per_launch": info["alg_bytes"], "kernel": "k_triangle<0,%d>" % warps}
 
     e2e = None
     if not args.no_e2e:
@@ -389,13 +397,13 @@ def run_eh(args):
         dst_p = torch.from_numpy(g["dst"]).pin_memory()
         ns, nd = src_p.numpy(), dst_p.numpy()
         e2e_steps = max(2, min(5, args.steps))
-        eh.Trie(ns, nd, g["n"], tau=args.tau).count("triangle")     # warm-up
+        eh.Trie(ns, nd, g["n"], tau=tau).count("triangle", xopts=xo)     # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ok = True
         for _ in range(e2e_steps):
-            t = eh.Trie(ns, nd, g["n"], tau=args.tau)
-            ok &= t.count("triangle") == gold["triangle"]
+            t = eh.Trie(ns, nd, g["n"], tau=tau)
+            ok &= t.count("triangle", xopts=xo) == gold["triangle"]
             t.close()
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
@@ -411,15 +419,18 @@ def run_eh(args):
 
     extra = {}
     if rank == 0 and args.workload in ("batch", "all"):
-        extra["batch"] = bench_batch(eh, args.tau)
+        extra["batch"] = bench_batch(eh)
     if rank == 0 and args.workload in ("serve", "all"):
-        extra["serve"] = bench_serve(eh, args.serve_queries, args.tau)
+        extra["serve"] = bench_serve(eh, args.serve_queries)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_vertices": g["n"], "m_unique_edges": m, "tau": args.tau,
+                "config": {"workload": WORKLOAD, "n_vertices": g["n"], "m_unique_edges": m, "tau": tau,
+                           "cta_warps": warps, "light_max": light_max,
+                           "tuning": "autotuned (paper_1503_02368_gb300/tuned.json)" if tuned and tau == tuned["tau"]
+                           else "fixed",
                            "count": count, "exact_vs_oracle": exact,
                            "l2": "flushed between timed steps (256 MiB write, outside the events)",
                            "parallelism": "replica per GPU" if world > 1 else "1 GPU"},

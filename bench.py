@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="triangle", choices=["triangle", "batch", "serve", "all"],
+    ap.add_argument("--workload", default="triangle", choices=["triangle", "clique4", "batch", "serve", "all"],
                     help="triangle: the headline line; batch/serve/all add the query-batch and serving results")
     ap.add_argument("--serve-queries", type=int, default=1500)
     return ap.parse_args()
@@ -208,6 +208,34 @@ def bench_batch(eh, tau=32, reps=3, log=None):
             "one_launch_per_query_s": t_one, "speedup": t_one / min(ts), "same_counts": ok,
             "exact_vs_oracle_sample": exact,
             "timing": "host wall clock around eh_count_batch (host subsets in, counts out), best of %d" % reps}
+
+
+def bench_clique4(eh, reps=5):
+    """Whole-graph 4-clique count on the Chung-Lu graph (n = 1e6, ~2e7 edges, gamma 2.1)."""
+    import torch
+    from synth import workloads as W
+    g = W.chunglu_1m()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))["chunglu_n1000000_g2.1"]
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    m = trie.stats()["n_edges"]
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    xo = eh.exec_opts(cta_warps=16)
+    for _ in range(2):
+        trie.count_async("clique4", out.data_ptr(), xopts=xo)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(reps):
+        trie.count_async("clique4", out.data_ptr(), xopts=xo)
+    s1.record()
+    torch.cuda.synchronize()
+    trie.status()
+    ms = s0.elapsed_time(s1) / reps
+    c = int(out.item())
+    trie.close()
+    return {"workload": "chunglu_n1000000_g2.1 (w_max 5e4, mean degree 40) 4-clique", "m_unique_edges": m,
+            "count": c, "exact_vs_oracle": c == gold["clique4"], "ms": ms, "edges_per_s": m / (ms / 1e3),
+            "cliques_per_s": c / (ms / 1e3), "tau": 32, "cta_warps": 16}
 
 
 def bench_serve(eh, n_queries=1500, tau=32, log=None):
@@ -418,6 +446,8 @@ def run_eh(args):
         cpu = cpu_baseline(g, args.cpu_seconds)
 
     extra = {}
+    if rank == 0 and args.workload in ("clique4", "batch", "all"):
+        extra["clique4"] = bench_clique4(eh)
     if rank == 0 and args.workload in ("batch", "all"):
         extra["batch"] = bench_batch(eh)
     if rank == 0 and args.workload in ("serve", "all"):

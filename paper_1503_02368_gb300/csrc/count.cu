@@ -309,6 +309,62 @@ struct StagedA {
     int amode;            // 0 bitmap in shared memory, 1 sorted in shared memory, 2 sorted in global memory
 };
 
+// A pair's plan against an on-chip bitmap A, computed by the lane that holds
+// the pair's descriptor: kind 1 = 128-bit AND over words [begin, end) of
+// `base`, kind 2 = B's elements [0, end) of `base` probe A, 0 = nothing.
+__device__ __forceinline__ void bitmap_plan(const TrieView &tv, uint32_t a_lo, uint32_t a_nw, const SetDesc &dv,
+                                            uint32_t &kind, int64_t &base, uint32_t &begin, uint32_t &end) {
+    kind = 0;
+    base = 0;
+    begin = end = 0;
+    if (dv.len == 0) return;
+    if (dv.nwords) {
+        const uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
+        const uint32_t ov = hi > lo ? hi - lo : 0;
+        if (ov <= dv.len) {
+            kind = ov ? 1u : 0u;
+            base = (int64_t)dv.woff - (int64_t)dv.lo_word;   // word w of B is words[base + w]
+            begin = lo;
+            end = hi;
+            return;
+        }
+    }
+    kind = 2;
+    base = (int64_t)dv.off;
+    end = dv.len;
+}
+
+template <int MODE>
+__device__ __forceinline__ void run_plan(const TrieView &tv, const uint32_t *sA, uint32_t a_lo, uint32_t a_nw,
+                                         uint32_t kind, int64_t base, uint32_t begin, uint32_t end, uint32_t duv,
+                                         Acc &acc, unsigned long long *vt) {
+    const uint32_t lane4 = (threadIdx.x & 31) * 4;
+    if (kind == 1) {
+        const uint32_t *bw = tv.words + base;
+        for (uint32_t i = begin + lane4; i < end; i += 128) {
+            const uint4 b = ldg4(bw + i);
+            const uint4 a = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
+            on_word<MODE>(acc, a.x & b.x, i * 32, duv, tv, vt);
+            on_word<MODE>(acc, a.y & b.y, i * 32 + 32, duv, tv, vt);
+            on_word<MODE>(acc, a.z & b.z, i * 32 + 64, duv, tv, vt);
+            on_word<MODE>(acc, a.w & b.w, i * 32 + 96, duv, tv, vt);
+        }
+    } else if (kind == 2) {
+        const uint32_t *bp = tv.nbr + base;
+        const uint32_t abase = a_lo * 32, nbits = a_nw * 32;
+        for (uint32_t p = lane4; p < end; p += 256) {
+            const uint4 e0 = ldg4(bp + p);
+            const uint4 e1 = p + 128 < end ? ldg4(bp + p + 128) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+            const uint32_t w[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint32_t x = w[c] - abase;
+                if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) on_match<MODE>(acc, w[c], duv, tv, vt);
+            }
+        }
+    }
+}
+
 // Returns false when the bounded wait for the bulk copy ran out (every thread
 // of the CTA then returns false; the caller must leave the kernel).
 template <int WARPS>
@@ -396,6 +452,21 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
             mine = tv.desc[vl];
         }
         const uint32_t nb = min(PAIR_BATCH, st.len - j0);
+        if (st.amode == 0 && MODE != M_VERTEX) {
+            // each descriptor lane plans its pair; the warp runs the plans in turn
+            uint32_t pk, pb, pe;
+            int64_t pbase;
+            bitmap_plan(tv, st.a_lo, st.a_nw, mine, pk, pbase, pb, pe);
+            const uint32_t pduv = du.deg + mine.deg;
+            for (uint32_t i = 0; i < nb; ++i) {
+                const uint32_t kind = __shfl_sync(FULL, pk, i);
+                if (kind == 0) continue;
+                run_plan<MODE>(tv, sA, st.a_lo, st.a_nw, kind, __shfl_sync(FULL, pbase, i),
+                               __shfl_sync(FULL, pb, i), __shfl_sync(FULL, pe, i),
+                               MODE == M_LOLLI ? __shfl_sync(FULL, pduv, i) : 0u, acc, vt);
+            }
+            continue;
+        }
         for (uint32_t i = 0; i < nb; ++i) {
             const uint32_t j = j0 + i;
             const uint32_t v = __shfl_sync(FULL, vl, i);

@@ -372,7 +372,8 @@ def run_eh(args):
     tau = args.tau if args.tau is not None else (tuned["tau"] if tuned else 32)
     warps = tuned["cta_warps"] if tuned and args.tau is None else 8
     light_max = tuned["light_max"] if tuned and args.tau is None else 32
-    xo = eh.exec_opts(cta_warps=warps, light_max=light_max)
+    ratio = tuned.get("gallop_ratio", 32) if tuned and args.tau is None else 32
+    xo = eh.exec_opts(cta_warps=warps, light_max=light_max, gallop_ratio=ratio)
     args.tau = tau
     trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
     st = trie.stats()
@@ -458,7 +459,7 @@ def run_eh(args):
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_vertices": g["n"], "m_unique_edges": m, "tau": tau,
-                           "cta_warps": warps, "light_max": light_max,
+                           "cta_warps": warps, "light_max": light_max, "gallop_ratio": ratio,
                            "tuning": "autotuned (paper_1503_02368_gb300/tuned.json)" if tuned and tau == tuned["tau"]
                            else "fixed",
                            "count": count, "exact_vs_oracle": exact,

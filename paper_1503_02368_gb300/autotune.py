@@ -64,8 +64,8 @@ def tune_batch(graph, patterns, offsets, pool, taus=DEFAULT_TAUS, warps=DEFAULT_
 
 
 def tune_whole(graph, pattern="triangle", taus=DEFAULT_TAUS, warps=DEFAULT_WARPS, light=DEFAULT_LIGHT, reps=3,
-               log=None):
-    """Best (tau, cta_warps, light_max) for a whole-graph count."""
+               log=None, ratios=(32,)):
+    """Best (tau, cta_warps, light_max, gallop_ratio) for a whole-graph count."""
     import torch
     trials = []
     ref = None
@@ -74,17 +74,18 @@ def tune_whole(graph, pattern="triangle", taus=DEFAULT_TAUS, warps=DEFAULT_WARPS
         trie = _eh.Trie(graph["src"], graph["dst"], graph["n"], tau=tau)
         for w in warps:
             for lm in light:
-                xo = _eh.exec_opts(cta_warps=w, light_max=lm)
-                t = _time(lambda: trie.count_async(pattern, out.data_ptr(), xopts=xo), reps)
-                trie.status()
-                c = int(out.item())
-                if ref is None:
-                    ref = c
-                if c != ref:
-                    raise RuntimeError("counts differ between tuning settings")
-                trials.append({"tau": tau, "cta_warps": w, "light_max": lm, "seconds": t})
-                if log:
-                    log(trials[-1])
+                for r in ratios:
+                    xo = _eh.exec_opts(cta_warps=w, light_max=lm, gallop_ratio=r)
+                    t = _time(lambda: trie.count_async(pattern, out.data_ptr(), xopts=xo), reps)
+                    trie.status()
+                    c = int(out.item())
+                    if ref is None:
+                        ref = c
+                    if c != ref:
+                        raise RuntimeError("counts differ between tuning settings")
+                    trials.append({"tau": tau, "cta_warps": w, "light_max": lm, "gallop_ratio": r, "seconds": t})
+                    if log:
+                        log(trials[-1])
         trie.close()
     best = min(trials, key=lambda r: r["seconds"])
     return best, trials

@@ -47,6 +47,7 @@ eh_status check_status(eh_trie *t, cudaStream_t s) {
 // enqueue one whole-graph count; result left in d_out (device)
 eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
                         unsigned long long *d_out) {
+    NvtxRange nv("eh_count");
     WorkPlan *plan = nullptr;
     EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
     unsigned long long *sc = t->d_scratch;

@@ -287,6 +287,7 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     const uint32_t nq = (uint32_t)sel.size();
     if (nq == 0) return EH_OK;
     const double t_begin = now_s();
+    NvtxRange nv("eh_count_batch: prepare + count");
     Scratch sc(s);
     const uint32_t n = t->n;
     // host tables

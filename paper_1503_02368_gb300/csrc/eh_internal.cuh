@@ -12,6 +12,13 @@
 #include <map>
 
 #include "eh.h"
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range for the lifetime of a scope (visible in Nsight Systems / Compute)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ------------------------------------------------------------------ errors
 

@@ -114,6 +114,7 @@ eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan *
     std::lock_guard<std::mutex> g(t->mu);
     auto it = t->plans.find(light_max);
     if (it != t->plans.end()) { *out = &it->second; return EH_OK; }
+    NvtxRange nv("eh work plan");
     WorkPlan p;
     p.light_max = light_max;
     TrieView tv = t->view();

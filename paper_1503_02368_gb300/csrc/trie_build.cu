@@ -465,6 +465,7 @@ extern "C" eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uin
     o.flags = 0;
     if (opts) o = *opts;
     cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange nv("eh_build_trie");
     eh_trie *t = new (std::nothrow) eh_trie();
     if (!t) { eh_set_error("host allocation failed"); return EH_ENOMEM; }
     t->n = n_vertices;

@@ -228,3 +228,45 @@ def test_bounded_wait_reports_timeout_and_context_survives(eh):
     g = W.er_10k_100k()
     t = eh.Trie(g["src"], g["dst"], g["n"])
     assert t.count("triangle") == GOLD["er_n10000_m100000"]["triangle"]
+
+
+def test_device_input_build_matches_host_build(eh):
+    import torch
+    g = W.rmat_graph(13, 1503 + 13)
+    host = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    s = torch.from_numpy(g["src"].astype(np.int32)).cuda()
+    d = torch.from_numpy(g["dst"].astype(np.int32)).cuda()
+    dev = eh.Trie(s, d, g["n"], tau=32)
+    for p in PATS:
+        assert dev.count(p) == host.count(p)
+    assert dev.stats()["n_edges"] == host.stats()["n_edges"]
+
+
+def test_sparse_large_id_space(eh):
+    # 2^24 ids, a few thousand edges spread over the whole range (24-bit keys)
+    rng = np.random.default_rng(17)
+    n = 1 << 24
+    ids = rng.choice(n, 3000, replace=False).astype(np.uint32)
+    e = [(int(ids[i]), int(ids[j])) for i, j in rng.integers(0, 3000, size=(20000, 2))]
+    e += [(int(ids[i]), int(ids[j])) for i in range(40) for j in range(i + 1, 40)]   # a 40-clique
+    s, d = G.arrays(e)
+    o = oracle.Graph(n, s, d)
+    t = eh.Trie(s, d, n, tau=32)
+    for p in PATS:
+        assert t.count(p) == o.count(p), p
+    S = ids[:40]
+    assert t.count("clique4", subset=S) == math.comb(40, 4)
+
+
+def test_star_plus_clique_skew(eh):
+    # one vertex adjacent to everything (degree n-1) next to a dense core:
+    # every pruned set of the core contains the hub; tests both CTA and warp paths
+    n = 5000
+    e = [(0, v) for v in range(1, n)] + [(i, j) for i in range(1, 60) for j in range(i + 1, 60)]
+    s, d = G.arrays(e)
+    o = oracle.Graph(n, s, d)
+    for tau in (0, 32, 0xFFFFFFFF):
+        t = eh.Trie(s, d, n, tau=tau)
+        assert t.count("triangle") == math.comb(59, 2) + math.comb(59, 3)
+        for p in PATS:
+            assert t.count(p) == o.count(p), (p, tau)

@@ -228,6 +228,12 @@ eh_status eh_trie_export(const eh_trie *trie, uint32_t which, uint32_t *new_to_o
 
 void eh_free_trie(eh_trie *trie);
 
+/* eh_test_fail_alloc_after -- failure injection for tests: the n-th device
+ * allocation the library makes from now on (n = 0: the next one) fails as if
+ * the device were out of memory; n < 0 disarms.  Calls then return
+ * EH_ENOMEM and release what they had allocated. */
+void eh_test_fail_alloc_after(long long n);
+
 /* eh_selftest_wait_timeout -- runs one kernel that waits, with the bounded
  * wait every count kernel uses for its bulk copies, on a barrier phase that
  * nothing completes.  The wait gives up after limit_us microseconds and the

@@ -2,6 +2,7 @@
 #include "eh_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 namespace {
@@ -74,6 +75,18 @@ eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &x
 }
 
 eh_status eh_check_status(eh_trie *t, cudaStream_t s) { return check_status(t, s); }
+
+namespace {
+std::atomic<long long> g_fail_countdown{-1};
+}
+
+bool eh_alloc_should_fail() {
+    long long c = g_fail_countdown.load(std::memory_order_relaxed);
+    if (c < 0) return false;
+    return g_fail_countdown.fetch_sub(1) == 0;
+}
+
+extern "C" void eh_test_fail_alloc_after(long long n) { g_fail_countdown.store(n < 0 ? -1 : n); }
 
 void eh_set_error(const char *fmt, ...) {
     va_list ap;

@@ -425,9 +425,9 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
 
 constexpr uint32_t PAIR_BATCH = 4;   // pairs a warp takes at a time from its CTA's vertex
 
-__device__ __forceinline__ uint32_t next_j(uint32_t *s_next) {
+__device__ __forceinline__ uint32_t next_j(uint32_t *s_next, uint32_t batch = PAIR_BATCH) {
     uint32_t j = 0;
-    if ((threadIdx.x & 31) == 0) j = atomicAdd(s_next, PAIR_BATCH);
+    if ((threadIdx.x & 31) == 0) j = atomicAdd(s_next, batch);
     return __shfl_sync(FULL, j, 0);
 }
 
@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
 // same layout-dispatched intersection as the triangle on (S_<z, N+(z)).
 
 constexpr uint32_t S_CAP = 1024;   // per-warp shared S buffer (elements)
+constexpr uint32_t K4_PAIR_BATCH = 1;   // (x, y) pairs are heavy and uneven: one at a time
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t &total) {
     const int lane = threadIdx.x & 31;
@@ -784,12 +785,12 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
     StagedA st;
     if (!stage_set<WARPS>(tv, dx, sA, mbar, phase, st, status)) return false;
     for (;;) {
-        const uint32_t j0 = next_j(s_next);
+        const uint32_t j0 = next_j(s_next, K4_PAIR_BATCH);
         if (j0 >= st.len) break;
         const uint32_t jl = j0 + lane;
         SetDesc mine = empty_desc();
-        if (lane < PAIR_BATCH && jl < st.len) mine = tv.desc[st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl]];
-        const uint32_t nbat = min(PAIR_BATCH, st.len - j0);
+        if (lane < K4_PAIR_BATCH && jl < st.len) mine = tv.desc[st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl]];
+        const uint32_t nbat = min(K4_PAIR_BATCH, st.len - j0);
         for (uint32_t i = 0; i < nbat; ++i) {
         const uint32_t j = j0 + i;
         const SetDesc dy = bcast_desc(mine, i);
@@ -1027,6 +1028,7 @@ eh_status launch_k4(eh_trie *t, const WorkPlan &plan, TrieView tv, const eh_exec
             cudaFree(t->d_arena);
             t->d_arena = nullptr;
             t->arena_words = 0;
+            if (eh_alloc_should_fail()) { eh_set_error("arena allocation failed (injected)"); return EH_ENOMEM; }
             EH_CUDA_TRY(cudaMalloc((void **)&t->d_arena, need * 4));
             t->arena_words = need;
         }

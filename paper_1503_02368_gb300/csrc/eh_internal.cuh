@@ -151,11 +151,19 @@ eh_status dev_exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, 
 // (the two buffers may be swapped on return).
 eh_status dev_radix_sort_u64(uint64_t **keys, uint64_t **tmp, uint64_t n, int key_bits, cudaStream_t s);
 
+// Allocation-failure injection for tests (eh_test_fail_alloc_after): when
+// armed, the countdown-th device allocation from now fails as if out of memory.
+bool eh_alloc_should_fail();
+
 // Device memory helpers (stream-ordered).
 template <typename T>
 eh_status dev_alloc(T **p, uint64_t count, cudaStream_t s) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (eh_alloc_should_fail()) {
+        eh_set_error("device allocation of %llu bytes failed (injected)", (unsigned long long)(sizeof(T) * count));
+        return EH_ENOMEM;
+    }
     cudaError_t e = cudaMallocAsync((void **)p, sizeof(T) * count, s);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -94,7 +94,8 @@ eh_status make_list(TrieView tv, uint32_t n, int nb, uint32_t light_max, int cls
     }
     uint32_t *ids = nullptr;
     if (st == EH_OK) {
-        cudaError_t e = cudaMalloc((void **)&ids, (cnt ? cnt : 1) * 4);
+        cudaError_t e = eh_alloc_should_fail() ? cudaErrorMemoryAllocation
+                                               : cudaMalloc((void **)&ids, (cnt ? cnt : 1) * 4);
         if (e != cudaSuccess) { cudaGetLastError(); eh_set_error("work list allocation failed"); st = EH_ENOMEM; }
     }
     if (st == EH_OK && cnt) k_key_ids<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(k1, (uint32_t)cnt, nb, ids);

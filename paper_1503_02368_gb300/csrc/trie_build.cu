@@ -200,6 +200,10 @@ template <typename T>
 eh_status persist_alloc(T **p, uint64_t count, uint64_t *bytes) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (eh_alloc_should_fail()) {
+        eh_set_error("device allocation of %llu bytes failed (injected)", (unsigned long long)(sizeof(T) * count));
+        return EH_ENOMEM;
+    }
     cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
     if (e != cudaSuccess) {
         cudaGetLastError();

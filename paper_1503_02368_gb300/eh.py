@@ -64,7 +64,7 @@ class ServerStats(ctypes.Structure):
 
 EXPORTED = ["eh_build_trie", "eh_count", "eh_count_ex", "eh_count_noalloc", "eh_count_async", "eh_count_status", "eh_count_info_get",
             "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_batch_profile_get", "eh_trie_stats_get", "eh_trie_export",
-            "eh_free_trie", "eh_last_error", "eh_selftest_wait_timeout", "eh_server_create", "eh_server_submit", "eh_server_poll",
+            "eh_free_trie", "eh_last_error", "eh_selftest_wait_timeout", "eh_test_fail_alloc_after", "eh_server_create", "eh_server_submit", "eh_server_poll",
             "eh_server_wait", "eh_server_latency", "eh_server_stats_get", "eh_server_destroy"]
 
 
@@ -112,6 +112,8 @@ def lib():
     L.eh_trie_stats_get.argtypes = [vp, ctypes.POINTER(TrieStats)]
     L.eh_trie_export.restype = st
     L.eh_trie_export.argtypes = [vp, u32, u32p, u64p, u32p, u32p, u32p, u32p, u64p, u32p]
+    L.eh_test_fail_alloc_after.restype = None
+    L.eh_test_fail_alloc_after.argtypes = [ctypes.c_longlong]
     L.eh_selftest_wait_timeout.restype = st
     L.eh_selftest_wait_timeout.argtypes = [u32, vp]
     L.eh_free_trie.restype = None

@@ -270,3 +270,67 @@ def test_star_plus_clique_skew(eh):
         assert t.count("triangle") == math.comb(59, 2) + math.comb(59, 3)
         for p in PATS:
             assert t.count(p) == o.count(p), (p, tau)
+
+
+def test_injected_allocation_failures_release_everything(eh):
+    # each device allocation of a trie build, a work plan and a query batch
+    # fails in turn: the call returns EH_ENOMEM and keeps nothing allocated
+    import torch
+    L = eh.lib()
+    g = W.rmat_graph(12, 1503 + 12)
+    want = oracle.Graph(g["n"], g["src"], g["dst"]).triangles()
+    off, pool = synth.ego_subsets(g["n"], g["src"], g["dst"], synth.key(3, 3), 8, 0, 8, 512)
+    pats = ["triangle", "clique4"] * 4
+    ref_t = eh.Trie(g["src"], g["dst"], g["n"])
+    ref_b, _ = ref_t.count_batch(pats, off, pool)
+    ref_t.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    fails = {"build": 0, "plan": 0, "batch": 0}
+    try:
+        for k in range(200):                         # the trie build
+            L.eh_test_fail_alloc_after(k)
+            try:
+                t = eh.Trie(g["src"], g["dst"], g["n"])
+            except eh.EHError as e:
+                assert e.status == 2, str(e)
+                fails["build"] += 1
+                continue
+            L.eh_test_fail_alloc_after(-1)
+            assert t.count("triangle") == want
+            t.close()
+            break
+        for k in range(200):                         # the work plan (first count)
+            t = eh.Trie(g["src"], g["dst"], g["n"])
+            L.eh_test_fail_alloc_after(k)
+            try:
+                c = t.count("triangle")
+            except eh.EHError as e:
+                assert e.status == 2, str(e)
+                fails["plan"] += 1
+                L.eh_test_fail_alloc_after(-1)
+                assert t.count("triangle") == want   # the plan builds on the next call
+                t.close()
+                continue
+            L.eh_test_fail_alloc_after(-1)
+            assert c == want
+            t.close()
+            break
+        t = eh.Trie(g["src"], g["dst"], g["n"])
+        for k in range(300):                         # a query batch
+            L.eh_test_fail_alloc_after(k)
+            cb, sb = t.count_batch(pats, off, pool)
+            L.eh_test_fail_alloc_after(-1)
+            if sb.any():
+                assert set(sb.tolist()) == {2}
+                fails["batch"] += 1
+                continue
+            assert np.array_equal(cb, ref_b)
+            break
+        t.close()
+    finally:
+        L.eh_test_fail_alloc_after(-1)
+    assert fails["build"] > 10 and fails["plan"] > 2 and fails["batch"] > 10, fails
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < (64 << 20), (free0, free1)

@@ -553,6 +553,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
 
 constexpr uint32_t S_CAP = 1024;   // per-warp shared S buffer (elements)
 constexpr uint32_t K4_PAIR_BATCH = 1;   // (x, y) pairs are heavy and uneven: one at a time
+constexpr uint32_t SB_CAP_WORDS = 256;    // per-warp bitmap of S: value ranges up to 8,192
+constexpr uint32_t LANE_UINT_MAX = 64;    // a lane walks a uint N+(z) alone up to this length
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t &total) {
     const int lane = threadIdx.x & 31;
@@ -567,15 +569,22 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t &total) 
 }
 
 // S = A ∩ B, A an on-chip bitmap
+// S = A ∩ B, A an on-chip bitmap.  When B is a bitset and their overlap fits
+// the warp's bitmap buffer Sbm, the AND words are also written there (words
+// [lo, hi) at Sbm[0 ..)) and *bm_lo = lo, so level 2 need not rebuild S's
+// bitmap; otherwise *bm_lo = EH_PAD.
 __device__ uint32_t emit_bitmap(const TrieView &tv, const uint32_t *sA, uint32_t a_lo, uint32_t a_nw,
-                                const SetDesc &dv, uint32_t *S) {
+                                const SetDesc &dv, uint32_t *S, uint32_t *Sbm, uint32_t *bm_lo) {
     const int lane = threadIdx.x & 31;
     uint32_t ns = 0;
+    *bm_lo = EH_PAD;
     if (dv.nwords) {
         uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
         uint32_t ov = hi > lo ? hi - lo : 0;
         if (ov <= dv.len) {
             const uint32_t *bw = tv.words + dv.woff - dv.lo_word;
+            const bool keep = Sbm && ov <= SB_CAP_WORDS;
+            if (keep) *bm_lo = lo;
             for (uint32_t b0 = lo; b0 < hi; b0 += 128) {
                 uint32_t i = b0 + lane * 4;
                 uint32_t x[4] = {0, 0, 0, 0};
@@ -583,6 +592,7 @@ __device__ uint32_t emit_bitmap(const TrieView &tv, const uint32_t *sA, uint32_t
                     uint4 b = ldg4(bw + i);
                     uint4 a = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
                     x[0] = a.x & b.x; x[1] = a.y & b.y; x[2] = a.z & b.z; x[3] = a.w & b.w;
+                    if (keep) *reinterpret_cast<uint4 *>(Sbm + (i - lo)) = make_uint4(x[0], x[1], x[2], x[3]);
                 }
                 uint32_t cnt = __popc(x[0]) + __popc(x[1]) + __popc(x[2]) + __popc(x[3]), tot;
                 uint32_t pos = ns + warp_excl_scan(cnt, tot);
@@ -699,11 +709,9 @@ __device__ uint32_t emit_sorted(const TrieView &tv, const uint32_t *A, uint32_t 
 // whose N+(z) is a short uint array probes S's bitmap with each element.  The
 // remaining z's (and every z of a sparse S) run the warp-wide routines, z by
 // z, with their descriptors loaded one per lane beforehand.
-constexpr uint32_t SB_CAP_WORDS = 256;    // per-warp bitmap of S: value ranges up to 8,192
-constexpr uint32_t LANE_UINT_MAX = 64;    // a lane walks a uint N+(z) alone up to this length
 
 __device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t *S, uint32_t ns, uint32_t ratio,
-                                              uint32_t *Sbm, Acc &acc) {
+                                              uint32_t *Sbm, uint32_t bm_lo, Acc &acc) {
     const int lane = threadIdx.x & 31;
     uint32_t s_lo = 0, s_nw = 0;
     bool bm = false;
@@ -711,7 +719,10 @@ __device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t
         s_lo = (S[0] >> 7) << 2;
         s_nw = (((S[ns - 1] >> 5) + 1 - s_lo) + 3) & ~3u;
         bm = s_nw <= SB_CAP_WORDS && s_nw <= ns;
-        if (bm) {
+        if (bm && bm_lo != EH_PAD) {
+            // level 1 left S's words [bm_lo, ...) in Sbm: S's own range starts inside it
+            Sbm += s_lo - bm_lo;
+        } else if (bm) {
             for (uint32_t w = lane; w < s_nw; w += 32) Sbm[w] = 0u;
             __syncwarp();
             for (uint32_t k = lane; k < ns; k += 32) {
@@ -801,9 +812,11 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
             if (lane == 0) atomicOr(status, DEV_ST_INVALID);
             continue;
         }
-        uint32_t ns = st.amode == 0 ? emit_bitmap(tv, sA, st.a_lo, st.a_nw, dy, S)
+        uint32_t *Sbm = sB + warp * SB_CAP_WORDS;
+        uint32_t bm_lo = EH_PAD;
+        uint32_t ns = st.amode == 0 ? emit_bitmap(tv, sA, st.a_lo, st.a_nw, dy, S, Sbm, &bm_lo)
                                     : emit_sorted(tv, st.A, j, dy, ratio, S);
-        clique_level2(tv, S, ns, ratio, sB + warp * SB_CAP_WORDS, acc);
+        clique_level2(tv, S, ns, ratio, Sbm, bm_lo, acc);
         __syncwarp();
         }
     }

@@ -95,3 +95,36 @@ def test_invalid_query_fails_alone(eh, setup):
     assert sg == 0 and cg == trie.count("triangle", subset=pool[off[1]:off[2]])
     assert sb == 1
     srv.close()
+
+
+def test_rmat24_serving_workload_matches_oracle(eh):
+    # the serving configuration itself: R-MAT scale 24 resident, ego nets with
+    # induced edges log-uniform in [100, 1e6], patterns triangle / 4-clique /
+    # lollipop; the oracle's counts of a sample of 24 queries (8 per pattern)
+    import json
+    import os
+    from tests.golden.make_golden import fingerprint
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "workload_counts.json")))
+    gold = gold["rmat_s24_serve"]
+    g = W.rmat24_serve(n_queries=gold["n_queries"])
+    assert fingerprint(g) == gold["fingerprint"]
+    names = ("triangle", "clique4", "lollipop")
+    off, pool = g["offsets"], g["pool"]
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    srv = eh.Server(trie, memory_budget_bytes=48 << 30, max_batch=32, max_inflight=3)
+    tickets = {}
+    for q in range(gold["n_queries"]):               # every query of the sample run, in the mix
+        while True:
+            t = srv.submit(names[g["patterns"][q]], pool[off[q]:off[q + 1]])
+            if t is not None:
+                break
+            time.sleep(0.001)
+        tickets[q] = t
+    for q, rec in gold["queries"].items():
+        c, st = srv.wait(tickets[int(q)], timeout_ms=600000)
+        assert st == 0 and rec["pattern"] == names[g["patterns"][int(q)]]
+        assert c == rec["count"], (q, rec)
+    for q in list(gold["queries"])[:6]:               # and alone
+        assert trie.count(gold["queries"][q]["pattern"], subset=pool[off[int(q)]:off[int(q) + 1]]) == \
+            gold["queries"][q]["count"]
+    srv.close()

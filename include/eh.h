@@ -24,6 +24,12 @@
  *     undirected).
  *   - Counts are exact uint64.  A count that would exceed 2^64-1 returns
  *     EH_EOVERFLOW.
+ *   - Concurrency: a trie is read-only after eh_build_trie.  Batches
+ *     (eh_count_batch*, subset counts, the server) own all their device state
+ *     and may run concurrently on different streams.  Whole-graph counts use
+ *     a small scratch area of the trie: eh_count/eh_count_ex serialise on it,
+ *     while eh_count_async calls on one trie must be issued on one stream (or
+ *     otherwise ordered) and not overlap an eh_count on the same trie.
  */
 #ifndef EH_H
 #define EH_H

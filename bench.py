@@ -232,10 +232,23 @@ def bench_clique4(eh, reps=5):
     trie.status()
     ms = s0.elapsed_time(s1) / reps
     c = int(out.item())
+    # the barbell by its two-node GHD plan on the same graph (per-vertex triangles, then the edge join)
+    trie.count_async("barbell", out.data_ptr())
+    torch.cuda.synchronize()
+    s0.record()
+    for _ in range(reps):
+        trie.count_async("barbell", out.data_ptr())
+    s1.record()
+    torch.cuda.synchronize()
+    trie.status()
+    ms_b = s0.elapsed_time(s1) / reps
+    cb = int(out.item())
     trie.close()
     return {"workload": "chunglu_n1000000_g2.1 (w_max 5e4, mean degree 40) 4-clique", "m_unique_edges": m,
             "count": c, "exact_vs_oracle": c == gold["clique4"], "ms": ms, "edges_per_s": m / (ms / 1e3),
-            "cliques_per_s": c / (ms / 1e3), "tau": 32, "cta_warps": 16}
+            "cliques_per_s": c / (ms / 1e3), "tau": 32, "cta_warps": 16,
+            "barbell": {"count": cb, "exact_vs_oracle": cb == gold.get("barbell"), "ms": ms_b,
+                        "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"}}
 
 
 def bench_serve(eh, n_queries=1500, tau=32, log=None):

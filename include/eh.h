@@ -57,12 +57,18 @@ typedef enum {
  *                relation, datalog join semantics (ordered tuples, w unconstrained):
  *                sum_x 2 t(x) d(x), with t(x) the triangles at x and d(x) its degree
  *   EH_LOLLIPOP_DISTINCT  lollipop subgraphs (triangle + pendant edge, w outside the
- *                triangle), each once: sum_x t(x) (d(x) - 2)                          */
+ *                triangle), each once: sum_x t(x) (d(x) - 2)
+ *   EH_BARBELL   Barbell(x,y,z,x',y',z') :- triangle at x, U(x,x'), triangle at x'
+ *                on the undirected relation, join semantics, by the two-node GHD
+ *                plan (triangles aggregated per vertex first, Sec. 3.1):
+ *                sum over ordered edges (x,x') of 2 t(x) * 2 t(x').  Whole graph
+ *                only (EH_EINVAL with a subset or in a batch).                    */
 typedef enum {
     EH_TRIANGLE = 0,
     EH_CLIQUE4 = 1,
     EH_LOLLIPOP = 2,
-    EH_LOLLIPOP_DISTINCT = 3
+    EH_LOLLIPOP_DISTINCT = 3,
+    EH_BARBELL = 4
 } eh_pattern;
 
 typedef struct eh_trie eh_trie; /* opaque, device-resident, owned by the library */

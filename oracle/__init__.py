@@ -51,6 +51,8 @@ def lib():
             f.restype = ctypes.c_uint64
             f.argtypes = [vp, ctypes.c_int, ip]
         L.oracle_vertex_triangles.argtypes = [vp, u32p, ctypes.c_uint64, u64p]
+        L.oracle_barbell.restype = ctypes.c_uint64
+        L.oracle_barbell.argtypes = [vp, ip]
         L.oracle_triangles_outer.restype = ctypes.c_uint64
         L.oracle_triangles_outer.argtypes = [vp, u32p, ctypes.c_uint64, ctypes.c_int, u64p, ip]
         L.oracle_induced.restype = vp
@@ -154,10 +156,14 @@ class Graph:
         o = ctypes.c_int(0)
         return self._chk(lib().oracle_lollipop_distinct(self._h, _threads(nthreads), ctypes.byref(o)), o)
 
+    def barbell(self, nthreads=1):
+        o = ctypes.c_int(0)
+        return self._chk(lib().oracle_barbell(self._h, ctypes.byref(o)), o)
+
     def count(self, pattern, nthreads=1):
-        """pattern: 'triangle' | 'clique4' | 'lollipop' | 'lollipop_distinct'."""
+        """pattern: 'triangle' | 'clique4' | 'lollipop' | 'lollipop_distinct' | 'barbell'."""
         return {"triangle": self.triangles, "clique4": self.clique4, "lollipop": self.lollipop,
-                "lollipop_distinct": self.lollipop_distinct}[pattern](nthreads=nthreads)
+                "lollipop_distinct": self.lollipop_distinct, "barbell": self.barbell}[pattern](nthreads=nthreads)
 
     def vertex_triangles(self, verts):
         verts = np.ascontiguousarray(verts, np.uint32)

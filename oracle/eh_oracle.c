@@ -365,6 +365,35 @@ void oracle_vertex_triangles(void *h, const uint32_t *verts, uint64_t k, uint64_
     }
 }
 
+/* ------------------------------------------------------------- barbell
+ * Table 1's Barbell(x,y,z,x',y',z') :- R(x,y),S(y,z),T(x,z),U(x,x'),
+ * R'(x',y'),S'(y',z'),T'(x',z') on the symmetric relation, COUNT(*) with join
+ * semantics, by the two-node GHD plan of Sec. 3.1 (Fig. barbell GHD): each
+ * triangle node is aggregated first (the ordered (y,z) pairs at x number
+ * 2 t(x)), then the root node joins U(x,x') on the aggregates:
+ *   B = sum_x sum_{x' in N(x)} (2 t(x)) (2 t(x')). */
+uint64_t oracle_barbell(void *h, int *overflow) {
+    oracle_graph *g = (oracle_graph *)h;
+    uint64_t *t = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)g->n + 1));
+    uint32_t *all = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)g->n + 1));
+    if (!t || !all) { free(t); free(all); if (overflow) *overflow = 1; return 0; }
+    for (uint32_t v = 0; v < g->n; ++v) all[v] = v;
+    oracle_vertex_triangles(h, all, g->n, t);
+    uint64_t b = 0;
+    int o = 0;
+    for (uint32_t x = 0; x < g->n; ++x) {
+        for (uint64_t i = g->off[x]; i < g->off[x + 1]; ++i) {
+            uint64_t term;
+            if (__builtin_mul_overflow(2 * t[x], 2 * t[g->adj[i]], &term)) o = 1;
+            if (__builtin_add_overflow(b, term, &b)) o = 1;
+        }
+    }
+    free(t);
+    free(all);
+    if (overflow) *overflow = o;
+    return b;
+}
+
 /* ------------------------------------------------- induced subgraph G[S]
  * The query restricted to a vertex subset: keep the edges whose both ends
  * lie in S (ids keep their meaning; S may be unsorted or repeat ids).

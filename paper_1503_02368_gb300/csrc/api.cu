@@ -25,8 +25,31 @@ __global__ void k_finalize(const unsigned long long *acc, int pattern, unsigned 
             r = 2ull * S;
             break;
         case EH_LOLLIPOP_DISTINCT: r = S - 6ull * T; break;
+        case EH_BARBELL: r = acc[SC_K4]; break;
     }
     *out = r;
+}
+
+// Barbell root node: B += 4 t(x) sum_{x' in N(x)} t(x'), one warp per vertex
+// over the symmetric trie (t = per-vertex triangle counts, new ids)
+__global__ void k_barbell(const unsigned long long *__restrict__ vt, const uint64_t *__restrict__ soff,
+                          const uint32_t *__restrict__ snbr, const uint32_t *__restrict__ deg, uint32_t n,
+                          unsigned long long *acc, uint32_t *status) {
+    const uint32_t x = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (x >= n) return;
+    const unsigned long long tx = vt[x];
+    if (tx == 0) return;
+    unsigned long long sum = 0;
+    const uint64_t b = soff[x];
+    for (uint32_t i = lane; i < deg[x]; i += 32) sum += vt[snbr[b + i]];
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (lane == 0 && sum) {
+        const unsigned long long hi = __umul64hi(4ull * tx, sum);
+        const unsigned long long term = 4ull * tx * sum;
+        const unsigned long long old = atomicAdd(acc, term);
+        if (hi || (tx >> 61) || old + term < old) atomicOr(status, DEV_ST_OVERFLOW);
+    }
 }
 
 __global__ void k_vt_to_old(const unsigned long long *vt, const uint32_t *new2old, uint32_t n, unsigned long long *out) {
@@ -53,7 +76,21 @@ eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, 
     EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
     unsigned long long *sc = t->d_scratch;
     EH_CUDA_TRY(cudaMemsetAsync(sc, 0, 8 * sizeof(unsigned long long), s));
-    if (pattern == EH_CLIQUE4) {
+    if (pattern == EH_BARBELL) {
+        // node 1 and 2 of the GHD: per-vertex triangle counts; root: the U(x,x') pass
+        unsigned long long *vt = nullptr;
+        EH_TRY(dev_alloc(&vt, t->n, s));
+        eh_status st = EH_OK;
+        if (cudaMemsetAsync(vt, 0, (uint64_t)(t->n ? t->n : 1) * 8, s) != cudaSuccess) st = EH_ECUDA;
+        if (st == EH_OK)
+            st = eh_launch_triangle(t, *plan, t->view(), M_VERTEX, xo, s, sc + SC_T, sc + SC_CNT, t->d_status, vt,
+                                    nullptr);
+        if (st == EH_OK && t->n)
+            k_barbell<<<(t->n + 7) / 8, 256, 0, s>>>(vt, t->d_soff, t->d_snbr, t->d_deg, t->n, sc + SC_K4,
+                                                       t->d_status);
+        dev_free(vt, s);
+        EH_TRY(st);
+    } else if (pattern == EH_CLIQUE4) {
         EH_TRY(eh_launch_clique4(t, *plan, t->view(), xo, s, sc + SC_K4, sc + SC_CNT2, t->d_status, nullptr, 0));
     } else {
         int mode = pattern == EH_TRIANGLE ? M_COUNT : M_LOLLI;
@@ -65,7 +102,7 @@ eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, 
     return EH_OK;
 }
 
-bool valid_pattern(int p) { return p >= EH_TRIANGLE && p <= EH_LOLLIPOP_DISTINCT; }
+bool valid_pattern(int p) { return p >= EH_TRIANGLE && p <= EH_BARBELL; }
 
 }  // namespace
 
@@ -132,7 +169,10 @@ extern "C" eh_status eh_count_ex(const eh_trie *trie, eh_pattern pattern, const 
                                  uint32_t subset_len, const eh_exec_opts *xopts, void *stream, uint64_t *out_count) {
     if (!trie || !out_count) { eh_set_error("eh_count: NULL argument"); return EH_EINVAL; }
     if (!valid_pattern(pattern)) { eh_set_error("eh_count: unknown pattern %d", (int)pattern); return EH_EINVAL; }
-    if (subset && subset_len) return eh_count_subset(trie, pattern, subset, subset_len, xopts, stream, out_count);
+    if (subset && subset_len) {
+        if (pattern == EH_BARBELL) { eh_set_error("eh_count: barbell is whole-graph only"); return EH_EINVAL; }
+        return eh_count_subset(trie, pattern, subset, subset_len, xopts, stream, out_count);
+    }
     eh_trie *t = const_cast<eh_trie *>(trie);
     cudaStream_t s = (cudaStream_t)stream;
     eh_exec_opts xo = eh_exec_defaults(xopts);

@@ -510,7 +510,7 @@ extern "C" eh_status eh_count_batch_ex(const eh_trie *trie, const eh_query *quer
     for (uint32_t i = 0; i < n_queries; ++i) {
         out_counts[i] = 0;
         const eh_query &q = queries[i];
-        bool ok = q.pattern <= EH_LOLLIPOP_DISTINCT &&
+        bool ok = (q.pattern <= EH_LOLLIPOP_DISTINCT || (q.pattern == EH_BARBELL && q.subset_len == 0)) &&
                   (q.subset_len == 0 || (subset_pool && q.subset_off + q.subset_len <= pool_len &&
                                          q.subset_off + q.subset_len >= q.subset_off));
         out_status[i] = ok ? EH_OK : EH_EINVAL;

@@ -138,7 +138,7 @@ extern "C" eh_status eh_server_create(const eh_trie *trie, uint64_t memory_budge
 extern "C" eh_status eh_server_submit(eh_server *s, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
                                       uint64_t *ticket) {
     if (!s || !ticket || (subset_len && !subset)) { eh_set_error("eh_server_submit: NULL argument"); return EH_EINVAL; }
-    if (pattern < EH_TRIANGLE || pattern > EH_LOLLIPOP_DISTINCT) {
+    if (pattern < EH_TRIANGLE || pattern > EH_BARBELL || (pattern == EH_BARBELL && subset_len)) {
         eh_set_error("eh_server_submit: unknown pattern");
         return EH_EINVAL;
     }

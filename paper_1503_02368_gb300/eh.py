@@ -12,7 +12,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libeh.so")
 _lib = None
 
-PATTERNS = {"triangle": 0, "clique4": 1, "lollipop": 2, "lollipop_distinct": 3}
+PATTERNS = {"triangle": 0, "clique4": 1, "lollipop": 2, "lollipop_distinct": 3, "barbell": 4}
 STATUS = {0: "EH_OK", 1: "EH_EINVAL", 2: "EH_ENOMEM", 3: "EH_ECUDA", 4: "EH_ETIMEOUT", 5: "EH_EOVERFLOW",
           6: "EH_EBUSY"}
 EH_BUILD_DEVICE_INPUT = 1

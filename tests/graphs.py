@@ -122,3 +122,17 @@ def bf_lollipop_distinct(A):
                 if w not in tri and A[v, w]:
                     c += 1
     return c
+
+
+def bf_barbell(A):
+    """COUNT(*) of the barbell join by enumerating (x, y, z, x', y', z')."""
+    n = len(A)
+    tri = [[(y, z) for y in range(n) for z in range(n) if A[x, y] and A[y, z] and A[x, z]] for x in range(n)]
+    c = 0
+    for x in range(n):
+        for x2 in range(n):
+            if A[x, x2]:
+                for _ in tri[x]:
+                    for _ in tri[x2]:
+                        c += 1
+    return c

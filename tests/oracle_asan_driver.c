@@ -18,6 +18,7 @@ void *oracle_induced(void *, const uint32_t *, uint64_t);
 int oracle_layout_is_bitset(const uint32_t *, uint64_t, uint32_t);
 void oracle_degree_order(void *, uint32_t *);
 uint64_t oracle_triangles_outer(void *, const uint32_t *, uint64_t, int, uint64_t *, int *);
+uint64_t oracle_barbell(void *, int *);
 
 static int fails = 0;
 #define CHECK(c)                                                     \
@@ -50,6 +51,8 @@ int main(void) {
         CHECK(oracle_clique4(g, 1, 2, &o) == c4);
         CHECK(oracle_clique4(g, 0, 1, &o) == 24 * c4);
         CHECK(n < 3 || oracle_lollipop(g, 2, &o) == (uint64_t)n * (n - 1) * (n - 2) * (n - 1));
+        CHECK(oracle_barbell(g, &o) == (uint64_t)n * (n - 1) * (n >= 3 ? (uint64_t)(n - 1) * (n - 2) : 0) *
+                                           (n >= 3 ? (uint64_t)(n - 1) * (n - 2) : 0) && !o);
         uint64_t ed = 0;
         uint32_t *all = malloc(4 * (n + 1));
         for (uint32_t i = 0; i < n; ++i) all[i] = i;

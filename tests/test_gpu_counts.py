@@ -334,3 +334,36 @@ def test_injected_allocation_failures_release_everything(eh):
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
     assert free0 - free1 < (64 << 20), (free0, free1)
+
+
+# ------------------------------------------------------------------ barbell (two-node GHD plan)
+
+@pytest.mark.parametrize("seed", range(4))
+def test_barbell_random_graphs(eh, seed):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(10, 300))
+    e = G.random_graph(n, float(rng.choice([0.05, 0.2, 0.5])), rng)
+    for tau in (0, 32, 0xFFFFFFFF):
+        t, o = both(eh, n, e, tau)
+        assert t.count("barbell") == o.count("barbell"), tau
+
+
+def test_barbell_closed_forms_and_workloads(eh):
+    e = [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (0, 3)]
+    t, _ = both(eh, 6, e)
+    assert t.count("barbell") == 4 * 14
+    t, _ = both(eh, 7, G.complete(7))
+    assert t.count("barbell") == 7 * 6 * (2 * math.comb(6, 2)) ** 2
+    g = W.rmat_graph(16, 1503 + 16)
+    t = eh.Trie(g["src"], g["dst"], g["n"])
+    assert t.count("barbell") == GOLD["rmat_s16_ef16"]["barbell"]
+
+
+def test_barbell_is_whole_graph_only(eh):
+    t, _ = both(eh, 7, G.complete(7))
+    with pytest.raises(eh.EHError) as ei:
+        t.count("barbell", subset=np.arange(5, dtype=np.uint32))
+    assert ei.value.status == 1
+    c, s = t.count_batch(["barbell", "barbell"], np.array([0, 0, 3], np.uint64), np.arange(3, dtype=np.uint32))
+    assert s[0] == 0 and int(c[0]) == 7 * 6 * (2 * math.comb(6, 2)) ** 2   # whole graph in a batch
+    assert s[1] == 1                                                        # with a subset: refused

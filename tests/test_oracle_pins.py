@@ -251,3 +251,30 @@ def test_outer_sample_sums_to_whole():
     c1, e1 = g.triangles_outer(half[1])
     assert c0 + c1 == g.triangles() == G.bf_triangles(G.adjacency(n, e))
     assert e0 + e1 == g.m
+
+
+# ------------------------------------------------------------ barbell
+
+@pytest.mark.parametrize("seed", range(6))
+def test_barbell_vs_literal_join_and_matrix_form(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(4, 14))
+    e = G.random_graph(n, 0.5, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    want = G.bf_barbell(A)
+    assert g.barbell() == want
+    d3 = np.diag(A @ A @ A)                     # ordered (y, z) pairs closing a triangle at x
+    assert want == int((A * np.outer(d3, d3)).sum())
+
+
+def test_barbell_closed_forms():
+    # two triangles joined by one edge: 2 ordered edge directions x (2*1)*(2*1) at the bridge ends
+    e = [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (0, 3)]
+    g = og(6, e)
+    # t = 1 on every vertex; B = sum over ordered edges of 4 t(x) t(x') = 4 * 14
+    assert g.barbell() == 4 * 14
+    # K_n: every ordered edge (n(n-1)) times (2 C(n-1,2))^2
+    for n in (3, 4, 6):
+        assert og(n, G.complete(n)).barbell() == n * (n - 1) * (2 * math.comb(n - 1, 2)) ** 2
+    assert og(10, G.petersen()).barbell() == 0

@@ -55,6 +55,9 @@ def lib():
         L.oracle_barbell.argtypes = [vp, ip]
         L.oracle_triangles_outer.restype = ctypes.c_uint64
         L.oracle_triangles_outer.argtypes = [vp, u32p, ctypes.c_uint64, ctypes.c_int, u64p, ip]
+        for f in (L.oracle_list_triangles, L.oracle_list_clique4):
+            f.restype = ctypes.c_uint64
+            f.argtypes = [vp, u32p, ctypes.c_uint64]
         L.oracle_induced.restype = vp
         L.oracle_induced.argtypes = [vp, u32p, ctypes.c_uint64]
         L.oracle_layout_is_bitset.restype = ctypes.c_int
@@ -170,6 +173,17 @@ class Graph:
         out = np.empty(len(verts), np.uint64)
         lib().oracle_vertex_triangles(self._h, _u32p(verts), len(verts),
                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        return out
+
+    def list(self, pattern):
+        """Every triangle ('triangle') or 4-clique ('clique4') once, as rows of
+        ascending original ids, in the oracle's loop order: uint32 [k, 3|4]."""
+        fn, width = {"triangle": (lib().oracle_list_triangles, 3),
+                     "clique4": (lib().oracle_list_clique4, 4)}[pattern]
+        k = int(fn(self._h, None, 0))
+        out = np.empty((k, width), np.uint32)
+        if k:
+            fn(self._h, _u32p(out), k)
         return out
 
     def induced(self, subset):

@@ -19,6 +19,8 @@
  *     nest of Sec. 3.3.2, for the 4-clique and lollipop of Table 1;
  *   - the lollipop's tail atom U(x,w) aggregated early as the count d(x) of
  *     its w values (the COUNT(*) aggregation of Sec. 3.1, Table 1);
+ *   - listing (the same joins with the head variables kept, Table 1 without
+ *     COUNT): each triangle or 4-clique written once as a tuple of ids;
  *   - the set-level layout rule of Sec. 4.4 (bitset iff the set's range, in
  *     bits, is at most tau bits per element).
  *
@@ -392,6 +394,75 @@ uint64_t oracle_barbell(void *h, int *overflow) {
     free(all);
     if (overflow) *overflow = o;
     return b;
+}
+
+/* --------------------------------------------------------- listing
+ * The same joins with the head variables kept (Table 1's queries without the
+ * COUNT aggregation): every match of the innermost level becomes one tuple.
+ * The pruned loop nests bind x > y > z (> w) in original ids, so each
+ * triangle (4-clique) appears exactly once; it is written with its ids in
+ * ascending order, (z, y, x) (and (w, z, y, x)).  Tuples are produced in the
+ * loop order.  At most `cap` tuples are written; the return value is the
+ * number of tuples of the result. */
+uint64_t oracle_list_triangles(void *h, uint32_t *out, uint64_t cap) {
+    oracle_graph *g = (oracle_graph *)h;
+    uint64_t k = 0;
+    for (uint32_t x = 0; x < g->n; ++x) {
+        uint64_t nx;
+        const uint32_t *Nx = set_of(g, x, 1, &nx);
+        for (uint64_t i = 0; i < nx; ++i) {
+            const uint32_t y = Nx[i];
+            uint64_t ny;
+            const uint32_t *Ny = set_of(g, y, 1, &ny);
+            uint64_t a = 0, b = 0;   /* two-pointer merge of N+(x) and N+(y) */
+            while (a < nx && b < ny) {
+                if (Nx[a] < Ny[b]) ++a;
+                else if (Nx[a] > Ny[b]) ++b;
+                else {
+                    if (k < cap) { out[3 * k] = Nx[a]; out[3 * k + 1] = y; out[3 * k + 2] = x; }
+                    ++k; ++a; ++b;
+                }
+            }
+        }
+    }
+    return k;
+}
+
+uint64_t oracle_list_clique4(void *h, uint32_t *out, uint64_t cap) {
+    oracle_graph *g = (oracle_graph *)h;
+    uint64_t dmax = 0, k = 0;
+    for (uint32_t v = 0; v < g->n; ++v)
+        if (g->nless[v] > dmax) dmax = g->nless[v];
+    uint32_t *S = (uint32_t *)malloc(sizeof(uint32_t) * (dmax + 1));
+    if (!S) return 0;
+    for (uint32_t x = 0; x < g->n; ++x) {
+        uint64_t nx;
+        const uint32_t *Nx = set_of(g, x, 1, &nx);
+        for (uint64_t i = 0; i < nx; ++i) {
+            const uint32_t y = Nx[i];
+            uint64_t ny;
+            const uint32_t *Ny = set_of(g, y, 1, &ny);
+            uint64_t ns = merge_into(Nx, nx, Ny, ny, S);
+            for (uint64_t j = 0; j < ns; ++j) {
+                const uint32_t z = S[j];
+                uint64_t nz;
+                const uint32_t *Nz = set_of(g, z, 1, &nz);
+                uint64_t a = 0, b = 0;   /* S ∩ N+(z) */
+                while (a < ns && b < nz) {
+                    if (S[a] < Nz[b]) ++a;
+                    else if (S[a] > Nz[b]) ++b;
+                    else {
+                        if (k < cap) {
+                            out[4 * k] = S[a]; out[4 * k + 1] = z; out[4 * k + 2] = y; out[4 * k + 3] = x;
+                        }
+                        ++k; ++a; ++b;
+                    }
+                }
+            }
+        }
+    }
+    free(S);
+    return k;
 }
 
 /* ------------------------------------------------- induced subgraph G[S]

@@ -92,6 +92,14 @@ def bf_clique4(A):
     return c
 
 
+def bf_list(A, k):
+    """Every k-clique of the 0/1 matrix A as a sorted tuple, by enumerating
+    every k-subset in lexicographic order."""
+    n = len(A)
+    return [q for q in itertools.combinations(range(n), k)
+            if all(A[i, j] for i, j in itertools.combinations(q, 2))]
+
+
 def bf_lollipop(A):
     """COUNT(*) of R(x,y),S(y,z),T(x,z),U(x,w) over the symmetric relation,
     by enumerating x, y, z, w literally."""

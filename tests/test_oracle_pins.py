@@ -6,6 +6,7 @@ operand) breaks at least one of them: brute force on dense matrices,
 textbook closed forms, the symmetric-data multiples of App. A.1.2, the AGM
 bound of Sec. 2.1, and invariance under relabelling.
 """
+import itertools
 import math
 
 import numpy as np
@@ -278,3 +279,49 @@ def test_barbell_closed_forms():
     for n in (3, 4, 6):
         assert og(n, G.complete(n)).barbell() == n * (n - 1) * (2 * math.comb(n - 1, 2)) ** 2
     assert og(10, G.petersen()).barbell() == 0
+
+
+# ------------------------------------------------------------ listing
+
+def _rows(t):
+    return [tuple(int(v) for v in r) for r in t]
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("pattern,k", [("triangle", 3), ("clique4", 4)])
+def test_listing_vs_subset_enumeration(seed, pattern, k):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(5, 22))
+    e = G.random_graph(n, float(rng.choice([0.2, 0.5, 0.8])), rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    rows = g.list(pattern)
+    assert rows.shape == (g.count(pattern), k)
+    assert all(list(r) == sorted(r) and len(set(r)) == k for r in _rows(rows))   # ascending ids
+    assert sorted(_rows(rows)) == G.bf_list(A, k)                                # same set, no repeats
+
+
+def test_listing_closed_forms():
+    for n in (3, 5, 8):
+        g = og(n, G.complete(n))
+        assert sorted(_rows(g.list("triangle"))) == list(itertools.combinations(range(n), 3))
+        assert sorted(_rows(g.list("clique4"))) == list(itertools.combinations(range(n), 4))
+    assert og(10, G.petersen()).list("triangle").shape == (0, 3)
+    assert og(9, G.cycle(9)).list("clique4").shape == (0, 4)
+    # wheel W_n (n >= 4): the n triangles through the hub, no 4-clique
+    rows = sorted(_rows(og(8, G.wheel(7)).list("triangle")))
+    assert rows == sorted(tuple(sorted((0, i, i % 7 + 1))) for i in range(1, 8))
+
+
+def test_listing_loop_order_and_capacity():
+    import ctypes
+    g = og(6, G.complete(6))
+    rows = g.list("triangle")
+    # loop order of the nest: largest id (x) slowest, then y, then z
+    keys = [(r[2], r[1], r[0]) for r in _rows(rows)]
+    assert keys == sorted(keys)
+    # a buffer smaller than the result: the full size is returned, only `cap` rows written
+    buf = np.full((4, 3), 7, np.uint32)
+    k = oracle.lib().oracle_list_triangles(g._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), 2)
+    assert k == 20
+    assert _rows(buf[:2]) == _rows(rows[:2]) and (buf[2:] == 7).all()

@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="triangle", choices=["triangle", "clique4", "batch", "serve", "all"],
+    ap.add_argument("--workload", default="triangle", choices=["triangle", "clique4", "batch", "serve", "list", "all"],
                     help="triangle: the headline line; batch/serve/all add the query-batch and serving results")
     ap.add_argument("--serve-queries", type=int, default=1500)
     return ap.parse_args()
@@ -249,6 +249,41 @@ def bench_clique4(eh, reps=5):
             "cliques_per_s": c / (ms / 1e3), "tau": 32, "cta_warps": 16,
             "barbell": {"count": cb, "exact_vs_oracle": cb == gold.get("barbell"), "ms": ms_b,
                         "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"}}
+
+
+def bench_list(eh, trie, xo, alg_bytes, gold, reps=3):
+    """Triangle listing (eh_list) of the resident R-MAT-22 trie into a device
+    buffer of 3 x uint32 per triangle: count pass, scan, write pass."""
+    import torch
+    rows = gold["triangle"]
+    buf = torch.empty((rows, 3), dtype=torch.int32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    n = trie.list_into("triangle", buf.data_ptr(), rows, xopts=xo)       # warm-up
+    stream = torch.cuda.current_stream()
+    ms = []
+    for k in range(reps):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = trie.list_into("triangle", buf.data_ptr(), rows, xopts=xo, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = min(ms)
+    hbm, peak_kind = measured_peaks()
+    out_bytes = 12.0 * rows
+    achieved = (alg_bytes + out_bytes) / (t / 1e3) / 1e9
+    del buf, flush
+    torch.cuda.empty_cache()
+    return {"workload": WORKLOAD + " triangle listing (rows of 3 x uint32 original ids, ascending)",
+            "rows": n, "exact_vs_oracle_count": n == rows, "ms": t, "ms_all": ms,
+            "rows_per_s": n / (t / 1e3), "output_gb": out_bytes / 1e9,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                         "alg_bytes_per_call": alg_bytes + out_bytes,
+                         "alg_bytes_note": "one traversal's lower-bound bytes + 12 bytes per written row; "
+                                           "the call runs the traversal twice (count pass, write pass)"},
+            "timing": "CUDA events around eh_list (both passes, the scan and its 8-byte D2H), min of %d" % reps}
 
 
 def bench_serve(eh, n_queries=1500, tau=32, log=None):
@@ -460,6 +495,8 @@ def run_eh(args):
         cpu = cpu_baseline(g, args.cpu_seconds)
 
     extra = {}
+    if rank == 0 and args.workload in ("list", "all"):
+        extra["list"] = bench_list(eh, trie, xo, info["alg_bytes"], gold)
     if rank == 0 and args.workload in ("clique4", "batch", "all"):
         extra["clique4"] = bench_clique4(eh)
     if rank == 0 and args.workload in ("batch", "all"):

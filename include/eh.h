@@ -47,7 +47,8 @@ typedef enum {
     EH_ECUDA = 3,     /* a CUDA runtime error (message in eh_last_error) */
     EH_ETIMEOUT = 4,  /* a bounded device-side wait ran out; the context stays usable */
     EH_EOVERFLOW = 5, /* a count exceeds uint64 */
-    EH_EBUSY = 6      /* admission refused: the query does not fit the memory budget now */
+    EH_EBUSY = 6,     /* admission refused: the query does not fit the memory budget now */
+    EH_ECAPACITY = 7  /* an output buffer is smaller than the result (the size needed is returned) */
 } eh_status;
 
 /* Table 1 patterns, COUNT(*) semantics:
@@ -92,8 +93,15 @@ typedef struct {
     uint32_t gallop_ratio;  /* uint∩uint: gallop when |large| > ratio*|small| (Sec. 4.2's 32:1); default 32 */
     uint32_t light_max;     /* vertices with |N+(u)| <= light_max run one warp each; default 32 */
     uint32_t cta_warps;     /* warps per CTA for heavy vertices (4, 8 or 16); default 8 */
-    uint32_t flags;         /* reserved, 0 */
+    uint32_t flags;         /* EH_EXEC_* bits, 0 by default */
 } eh_exec_opts;
+
+/* eh_list staging of A = N+(u) for vertices taken by a whole CTA: by default
+ * the kernel keeps A on chip as a bitmap when its value range fits, else as a
+ * sorted array when it fits, else reads it from device memory.  These bits
+ * force the later forms (same rows, other code paths; the counts ignore them). */
+#define EH_EXEC_SORTED_A 1u /* never a bitmap: the sorted array (on chip when it fits) */
+#define EH_EXEC_GLOBAL_A 2u /* A read from device memory, not staged */
 
 typedef struct {
     uint32_t n_vertices;   /* id space */
@@ -194,6 +202,27 @@ eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, const eh_ex
 /* eh_vertex_triangles -- t(x), the number of triangles containing x, for
  * every original id x (host array of n_vertices uint64). */
 eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint64_t *out_t);
+
+/* eh_list -- the rows of Triangle(x,y,z) or 4Clique(x,y,z,w) (Table 1 with
+ * the head variables kept instead of COUNT(*)) over the whole graph, written
+ * to a device buffer.
+ *   pattern   EH_TRIANGLE (rows of 3 ids) or EH_CLIQUE4 (rows of 4); any
+ *             other pattern is EH_EINVAL.
+ *   d_out     device buffer of `capacity` rows, uint32, row-major; 4-byte
+ *             aligned for triangles, 16-byte aligned for 4-cliques.  Owned by
+ *             the caller.  NULL with capacity 0: only the size is computed.
+ *   out_n     host; receives the number of rows of the result (equal to
+ *             eh_count of the same pattern), also when the buffer is too small.
+ * Each triangle (4-clique) is one row holding its vertices' original ids in
+ * ascending order; the order of the rows is unspecified.  When the result has
+ * more rows than `capacity` the call writes nothing and returns EH_ECAPACITY
+ * (size the buffer with eh_count, or with a first call with d_out NULL).  The
+ * call synchronises `stream`; whole-graph counts of the same trie wait for it.
+ * Temporary device memory: 16 bytes per vertex with |N+(v)| >= 2, plus for
+ * 4-cliques whose max out-degree exceeds 512, max out-degree x 4 bytes per
+ * resident warp. */
+eh_status eh_list(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
+                  uint32_t *d_out, uint64_t capacity, uint64_t *out_n);
 
 /* eh_count_batch -- n_queries independent queries in one persistent launch.
  * Each query's count goes to out_counts[i] and its status to out_status[i]

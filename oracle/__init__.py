@@ -55,6 +55,8 @@ def lib():
         L.oracle_barbell.argtypes = [vp, ip]
         L.oracle_triangles_outer.restype = ctypes.c_uint64
         L.oracle_triangles_outer.argtypes = [vp, u32p, ctypes.c_uint64, ctypes.c_int, u64p, ip]
+        L.oracle_list_triangles_at.restype = ctypes.c_uint64
+        L.oracle_list_triangles_at.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64]
         for f in (L.oracle_list_triangles, L.oracle_list_clique4):
             f.restype = ctypes.c_uint64
             f.argtypes = [vp, u32p, ctypes.c_uint64]
@@ -184,6 +186,14 @@ class Graph:
         out = np.empty((k, width), np.uint32)
         if k:
             fn(self._h, _u32p(out), k)
+        return out
+
+    def list_triangles_at(self, x):
+        """The triangles containing vertex x, rows of ascending ids: uint32 [t(x), 3]."""
+        k = int(lib().oracle_list_triangles_at(self._h, x, None, 0))
+        out = np.empty((k, 3), np.uint32)
+        if k:
+            lib().oracle_list_triangles_at(self._h, x, _u32p(out), k)
         return out
 
     def induced(self, subset):

@@ -465,6 +465,39 @@ uint64_t oracle_list_clique4(void *h, uint32_t *out, uint64_t cap) {
     return k;
 }
 
+/* The triangles containing x, from the symmetric sets: for y in N(x), for
+ * z in N(x) ∩ N(y) with y < z, the row of {x, y, z} in ascending order.  At
+ * most `cap` rows are written; returns t(x). */
+uint64_t oracle_list_triangles_at(void *h, uint32_t x, uint32_t *out, uint64_t cap) {
+    oracle_graph *g = (oracle_graph *)h;
+    uint64_t nx, k = 0;
+    const uint32_t *Nx = set_of(g, x, 0, &nx);
+    for (uint64_t i = 0; i < nx; ++i) {
+        const uint32_t y = Nx[i];
+        uint64_t ny;
+        const uint32_t *Ny = set_of(g, y, 0, &ny);
+        uint64_t a = 0, b = 0;
+        while (a < nx && b < ny) {
+            if (Nx[a] < Ny[b]) ++a;
+            else if (Nx[a] > Ny[b]) ++b;
+            else {
+                const uint32_t z = Nx[a];
+                if (y < z) {
+                    if (k < cap) {
+                        uint32_t r0 = x, r1 = y, r2 = z, t;   /* y < z; place x */
+                        if (r0 > r1) { t = r0; r0 = r1; r1 = t; }
+                        if (r1 > r2) { t = r1; r1 = r2; r2 = t; }
+                        out[3 * k] = r0; out[3 * k + 1] = r1; out[3 * k + 2] = r2;
+                    }
+                    ++k;
+                }
+                ++a; ++b;
+            }
+        }
+    }
+    return k;
+}
+
 /* ------------------------------------------------- induced subgraph G[S]
  * The query restricted to a vertex subset: keep the edges whose both ends
  * lie in S (ids keep their meaning; S may be unsorted or repeat ids).

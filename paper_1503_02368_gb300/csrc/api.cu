@@ -65,6 +65,7 @@ eh_status check_status(eh_trie *t, cudaStream_t s) {
     if (st & DEV_ST_TIMEOUT) { eh_set_error("a bounded device wait timed out"); return EH_ETIMEOUT; }
     if (st & DEV_ST_OVERFLOW) { eh_set_error("count exceeds uint64"); return EH_EOVERFLOW; }
     if (st & DEV_ST_INVALID) { eh_set_error("invalid id on the device"); return EH_EINVAL; }
+    if (st & DEV_ST_RANGE) { eh_set_error("listing: the count and write passes disagree"); return EH_ECUDA; }
     return EH_OK;
 }
 

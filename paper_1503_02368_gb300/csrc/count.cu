@@ -20,13 +20,13 @@
 // a whole CTA whose warps share the staged A and take the v's dynamically;
 // lighter ones get one warp each, A held one element per lane.
 #include "eh_internal.cuh"
+#include "dev_util.cuh"
 
 namespace {
 
-constexpr uint32_t FULL = 0xffffffffu;
+using namespace ehd;
+
 constexpr uint32_t BM_CAP_WORDS = 8192;        // 32 KB on-chip bitmap: value ranges up to 262,144
-constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;          // bounded wait for a bulk copy: iterations
-constexpr uint64_t MBAR_TIME_LIMIT_NS = 2000000000ull;  // ... and wall time (2 s)
 
 enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2 };
 
@@ -34,57 +34,6 @@ struct Acc {
     unsigned long long t;   // triangles
     unsigned long long s;   // sum over triangles of d(a)+d(b)+d(c)  (lollipop)
 };
-
-__device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// ---------------------------------------------------------- bulk copy (TMA)
-
-__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
-                 : "memory");
-}
-
-// 1-D bulk copy global -> shared, completion counted on mbar (bytes % 16 == 0,
-// both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-        : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// true when the phase with the given parity completed within the limits
-// (an iteration count and a wall-time bound, whichever comes first)
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity,
-                                          uint64_t limit_ns = MBAR_TIME_LIMIT_NS) {
-    uint32_t done = 0;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 0; it < MBAR_SPIN_LIMIT && !done; ++it) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"(parity)
-            : "memory");
-        if (!done && (it & 63) == 63 && global_ns() - t0 > limit_ns) break;
-    }
-    return done != 0;
-}
 
 // --------------------------------------------------------------- matches
 
@@ -148,15 +97,6 @@ __device__ __forceinline__ void pair_bitmap(const TrieView &tv, const uint32_t *
             if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) on_match<MODE>(acc, w[c], duv, tv, vt);
         }
     }
-}
-
-// smallest index i in [lo, hi) with A[i] >= key (A sorted), or hi
-__device__ __forceinline__ uint32_t lower_bound(const uint32_t *A, uint32_t lo, uint32_t hi, uint32_t key) {
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (A[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
 }
 
 // Descriptor of lane `src` broadcast to the warp (descriptors of upcoming

@@ -44,6 +44,7 @@ enum : uint32_t {
     DEV_ST_TIMEOUT = 1u,   // a bounded mbarrier wait gave up
     DEV_ST_OVERFLOW = 2u,  // an accumulator passed 2^63
     DEV_ST_INVALID = 4u,   // an input id was out of range
+    DEV_ST_RANGE = 8u,     // a listing row fell outside the range its count pass gave it (not written)
 };
 
 // ------------------------------------------------------------ set layouts

@@ -1,0 +1,657 @@
+// list.cu -- triangle and 4-clique listing into a caller's device buffer (eh_list).
+//
+// The joins of the count path with their head variables kept (Table 1's
+// Triangle(x,y,z) and 4Clique(x,y,z,w) without the COUNT aggregation): every
+// match of the innermost level of the generic join (Algorithm 1) becomes one
+// output row, the caller's ids of the clique in ascending order.
+//
+// Work items are those of the count plan: a vertex u with |N+(u)| above the
+// light bound is taken by a CTA, which stages A = N+(u) on chip (a bitmap
+// when its value range fits, else the sorted array) and whose warps take the
+// v in A dynamically; a lighter u is taken by one warp holding A one element
+// per lane.  Two passes run the same traversal.  The first stores each item's
+// number of rows, an exclusive scan turns those into output ranges, and the
+// second writes the rows.  Inside an item the lanes of a warp take positions
+// from ballot / prefix-sum ranks and the warps of a CTA reserve runs from a
+// shared-memory cursor: the output is dense, needs no global atomics, and the
+// rows of an item fill exactly the range the first pass gave it.
+//
+// Per pair the intersection picks its algorithm from the layouts as the count
+// path does (Sec. 4.2): bitset ∩ bitset by word AND; uint ∩ bitset by bit
+// probes; uint ∩ uint by binary searches from the smaller side (the side whose
+// elements the lanes hold).  Every loop over a set runs in warp-uniform rounds
+// of 32 lanes so that the matches of a round can be ranked by one ballot or
+// one warp prefix sum.
+#include "eh_internal.cuh"
+#include "dev_util.cuh"
+
+#include <algorithm>
+
+namespace {
+
+using namespace ehd;
+
+constexpr uint32_t LIST_WARPS = 8;
+constexpr uint32_t LA_CAP_WORDS = 8192;   // on-chip A: bitmap words or sorted elements (32 KB)
+constexpr uint32_t S_CAP = 512;           // per-warp level-1 set of the 4-clique in shared memory
+
+enum { P_TRI = 3, P_K4 = 4 };   // row width
+
+struct ListArgs {
+    TrieView tv;
+    const uint32_t *new2old;
+    const uint32_t *heavy;
+    uint32_t n_heavy;
+    const uint32_t *light;
+    uint32_t n_light;
+    uint32_t ratio;
+    uint32_t arena_stride;                 // words per warp slot of the arena (4-clique, large S)
+    uint32_t flags;                        // EH_EXEC_SORTED_A / EH_EXEC_GLOBAL_A
+    unsigned int *next_item;               // heavy items taken so far
+    unsigned long long *cnt;               // count pass: rows per item (heavy items, then light)
+    const unsigned long long *offs;        // write pass: first row of each item (n_items + 1 entries)
+    uint32_t *out;                         // rows of width 3 or 4
+    unsigned long long cap;                // rows the buffer holds
+    uint32_t *arena;
+    uint32_t *status;
+};
+
+// Output state of one warp for the current item.
+struct Sink {
+    unsigned long long n;        // count pass: rows found by this warp
+    unsigned long long cur;      // write pass, light item: next row of the warp
+    unsigned long long *s_cur;   // write pass, heavy item: the CTA's cursor (shared memory); null if light
+    unsigned long long end;      // write pass: end of the item's range
+    uint32_t key[3];             // caller ids of the bound prefix: u, v (and z)
+};
+
+__device__ __forceinline__ void sort2(uint32_t &a, uint32_t &b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+template <int W>
+__device__ __forceinline__ void put_row(const ListArgs &a, const Sink &sk, unsigned long long pos, uint32_t w_new) {
+    if (pos >= sk.end || pos >= a.cap) {   // the two passes disagree: never write outside the item's range
+        atomicOr(a.status, DEV_ST_RANGE);
+        return;
+    }
+    uint32_t x0 = sk.key[0], x1 = sk.key[1], x2 = __ldg(&a.new2old[w_new]);
+    if (W == P_TRI) {
+        sort2(x0, x1); sort2(x1, x2); sort2(x0, x1);
+        uint32_t *o = a.out + 3 * pos;
+        o[0] = x0; o[1] = x1; o[2] = x2;
+    } else {
+        uint32_t x3 = sk.key[2];
+        sort2(x0, x1); sort2(x2, x3); sort2(x0, x2); sort2(x1, x3); sort2(x1, x2);
+        *reinterpret_cast<uint4 *>(a.out + 4 * pos) = make_uint4(x0, x1, x2, x3);
+    }
+}
+
+// first output row of a round whose matches total `total` (warp-uniform)
+template <bool EMIT>
+__device__ __forceinline__ unsigned long long reserve(Sink &sk, uint32_t total) {
+    if (!EMIT) {
+        sk.n += total;
+        return 0;
+    }
+    unsigned long long base = 0;
+    if (total) {
+        if (sk.s_cur) {
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(sk.s_cur, (unsigned long long)total);
+            base = __shfl_sync(FULL, base, 0);
+        } else {
+            base = sk.cur;
+            sk.cur += total;
+        }
+    }
+    return base;
+}
+
+// One round where each lane has at most one candidate w (hit = w matches).
+template <int W, bool EMIT>
+__device__ __forceinline__ void emit_one(const ListArgs &a, Sink &sk, bool hit, uint32_t w) {
+    const uint32_t b = __ballot_sync(FULL, hit);
+    const unsigned long long base = reserve<EMIT>(sk, __popc(b));
+    if (EMIT && hit) {
+        const uint32_t lane = threadIdx.x & 31;
+        put_row<W>(a, sk, base + __popc(b & ((1u << lane) - 1u)), w);
+    }
+}
+
+// exclusive warp prefix sum of x; total in *total
+__device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t &total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    total = __shfl_sync(FULL, incl, 31);
+    return incl - x;
+}
+
+// One round where each lane has four candidate values v[c], matching where bit c of m is set.
+template <int W, bool EMIT>
+__device__ __forceinline__ void emit_four(const ListArgs &a, Sink &sk, uint32_t m, const uint4 &v) {
+    const uint32_t k = __popc(m);
+    if (!EMIT) {
+        sk.n += __reduce_add_sync(FULL, k);
+        return;
+    }
+    uint32_t total;
+    const uint32_t r = warp_excl(k, total);
+    const unsigned long long base = reserve<EMIT>(sk, total);
+    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+    uint32_t i = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if ((m >> c) & 1u) put_row<W>(a, sk, base + r + i++, vv[c]);
+}
+
+// One round where each lane has four words of matches, x[c] standing for the values 32*(w0+c)+bit.
+template <int W, bool EMIT>
+__device__ __forceinline__ void emit_words(const ListArgs &a, Sink &sk, const uint4 &x, uint32_t w0) {
+    const uint32_t k = __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
+    if (!EMIT) {
+        sk.n += __reduce_add_sync(FULL, k);
+        return;
+    }
+    uint32_t total;
+    const uint32_t r = warp_excl(k, total);
+    const unsigned long long base = reserve<EMIT>(sk, total);
+    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+    uint32_t i = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t b = xs[c];
+        while (b) {
+            const uint32_t bit = __ffs(b) - 1;
+            b &= b - 1;
+            put_row<W>(a, sk, base + r + i++, (w0 + c) * 32 + bit);
+        }
+    }
+}
+
+// x in the set with descriptor d (bit probe of its bitset, else binary search of its uint array)
+__device__ __forceinline__ bool in_set(const TrieView &tv, const SetDesc &d, uint32_t x) {
+    if (d.nwords) {
+        const uint32_t r = x - d.lo_word * 32;
+        return r < d.nwords * 32 && ((__ldg(&tv.words[d.woff + (r >> 5)]) >> (r & 31)) & 1u);
+    }
+    const uint32_t *B = tv.nbr + d.off;
+    const uint32_t p = lower_bound(B, 0, d.len, x);
+    return p < d.len && __ldg(&B[p]) == x;
+}
+
+__device__ __forceinline__ SetDesc bcast_desc(const SetDesc &d, int src) {
+    SetDesc r;
+    r.off = __shfl_sync(FULL, d.off, src);
+    r.len = __shfl_sync(FULL, d.len, src);
+    r.deg = __shfl_sync(FULL, d.deg, src);
+    r.woff = __shfl_sync(FULL, d.woff, src);
+    r.lo_word = __shfl_sync(FULL, d.lo_word, src);
+    r.nwords = __shfl_sync(FULL, d.nwords, src);
+    return r;
+}
+
+// ------------------------------------------------------------ staged A
+
+struct StagedA {
+    uint32_t mode;        // 0 bitmap in shared memory, 1 sorted array in shared memory, 2 sorted array in global
+    uint32_t len;
+    uint32_t a_lo, a_nw;  // bitmap: first word (value / 32) and number of words
+    const uint32_t *Ag;   // the stored uint array of A
+    const uint32_t *A;    // sorted elements (modes 1, 2)
+};
+
+// Stages A = N+(u) for the CTA.  Returns false when the bounded wait for the
+// bulk copy ran out (every thread of the CTA gets false and must leave).
+__device__ bool stage_a(const TrieView &tv, const SetDesc &du, uint32_t flags, uint32_t *sA, uint64_t *mbar,
+                        uint32_t &phase, StagedA &st, uint32_t *status) {
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    st.len = du.len;
+    st.Ag = tv.nbr + du.off;
+    const uint32_t first = __ldg(&st.Ag[0]), last = __ldg(&st.Ag[st.len - 1]);
+    st.a_lo = (first >> 7) << 2;
+    st.a_nw = (((last >> 5) + 1 - st.a_lo) + 3) & ~3u;
+    bool copy = false;
+    const bool bitmap_ok = !(flags & (EH_EXEC_SORTED_A | EH_EXEC_GLOBAL_A));
+    if (flags & EH_EXEC_GLOBAL_A) {
+        st.mode = 2;
+    } else if (bitmap_ok && du.nwords && du.nwords <= LA_CAP_WORDS) {   // the stored bitset, copied as is
+        st.mode = 0;
+        st.a_lo = du.lo_word;
+        st.a_nw = du.nwords;
+        copy = true;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mbar, st.a_nw * 4);
+            bulk_g2s(sA, tv.words + du.woff, st.a_nw * 4, mbar);
+        }
+    } else if (bitmap_ok && st.a_nw <= LA_CAP_WORDS) {   // uint array re-encoded as a bitmap on chip
+        st.mode = 0;
+        for (uint32_t i = tid * 4; i < st.a_nw; i += nthr * 4)
+            *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        for (uint32_t i = tid; i < st.len; i += nthr) {
+            const uint32_t x = __ldg(&st.Ag[i]);
+            atomicOr(&sA[(x >> 5) - st.a_lo], 1u << (x & 31));
+        }
+    } else if (st.len <= LA_CAP_WORDS) {            // sorted array copied on chip
+        st.mode = 1;
+        copy = true;
+        if (tid == 0) {
+            const uint32_t bytes = ((st.len + 3) & ~3u) * 4;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mbar, bytes);
+            bulk_g2s(sA, st.Ag, bytes, mbar);
+        }
+    } else {
+        st.mode = 2;
+    }
+    if (copy) {
+        const bool ok = mbar_wait(mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
+            mbar_wait(mbar, phase ^ 1);   // drain the copy still in flight, bounded
+            return false;
+        }
+    } else {
+        __syncthreads();
+    }
+    st.A = st.mode == 2 ? st.Ag : sA;
+    return true;
+}
+
+// ------------------------------------------------- level-1 intersections
+//
+// A ∩ N+(v) for A staged by the CTA, v = A[j].  Each match w goes to
+// `out_fn(hit-round ...)`: the emit_* rounds above when listing triangles,
+// the collection of S when listing 4-cliques.  Matches come out in ascending
+// order of w in every branch (rounds walk the sets upwards, lanes in order).
+
+template <int W, bool EMIT, bool COLLECT>
+struct Level1 {
+    const ListArgs &a;
+    Sink &sk;
+    uint32_t *S;      // COLLECT: destination of the matches
+    uint32_t ns;      // COLLECT: matches so far
+
+    __device__ __forceinline__ void one(bool hit, uint32_t w) {
+        if (COLLECT) {
+            const uint32_t b = __ballot_sync(FULL, hit);
+            if (hit) S[ns + __popc(b & ((1u << (threadIdx.x & 31)) - 1u))] = w;
+            ns += __popc(b);
+        } else {
+            emit_one<W, EMIT>(a, sk, hit, w);
+        }
+    }
+    __device__ __forceinline__ void four(uint32_t m, const uint4 &v) {
+        if (COLLECT) {
+            uint32_t total;
+            const uint32_t r = warp_excl(__popc(m), total);
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+            uint32_t i = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if ((m >> c) & 1u) S[ns + r + i++] = vv[c];
+            ns += total;
+        } else {
+            emit_four<W, EMIT>(a, sk, m, v);
+        }
+    }
+    __device__ __forceinline__ void words(const uint4 &x, uint32_t w0) {
+        if (COLLECT) {
+            uint32_t total;
+            const uint32_t r = warp_excl(__popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w), total);
+            const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+            uint32_t i = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t b = xs[c];
+                while (b) {
+                    const uint32_t bit = __ffs(b) - 1;
+                    b &= b - 1;
+                    S[ns + r + i++] = (w0 + c) * 32 + bit;
+                }
+            }
+            ns += total;
+        } else {
+            emit_words<W, EMIT>(a, sk, x, w0);
+        }
+    }
+
+    // A as the on-chip bitmap of words [a_lo, a_lo + a_nw)
+    __device__ __forceinline__ void bitmap(const uint32_t *sA, uint32_t a_lo, uint32_t a_nw, const SetDesc &dv) {
+        const TrieView &tv = a.tv;
+        const uint32_t lane = threadIdx.x & 31;
+        if (dv.nwords) {
+            const uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
+            if (hi <= lo) return;   // disjoint value ranges
+            if (hi - lo <= dv.len) {   // fewer overlapping words than elements: bitset ∩ bitset
+                const uint32_t *bw = tv.words + dv.woff - dv.lo_word;
+                for (uint32_t i0 = lo; i0 < hi; i0 += 128) {
+                    const uint32_t i = i0 + lane * 4;
+                    uint4 x = make_uint4(0, 0, 0, 0);
+                    if (i < hi) {
+                        const uint4 b = ldg4(bw + i);
+                        const uint4 av = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
+                        x = make_uint4(av.x & b.x, av.y & b.y, av.z & b.z, av.w & b.w);
+                    }
+                    words(x, i);
+                }
+                return;
+            }
+        }
+        // uint N+(v): every element probes A's bitmap (the padding EH_PAD is out of range)
+        const uint32_t *bp = tv.nbr + dv.off;
+        const uint32_t base = a_lo * 32, nbits = a_nw * 32;
+        for (uint32_t p0 = 0; p0 < dv.len; p0 += 128) {
+            const uint32_t p = p0 + lane * 4;
+            const uint4 e = p < dv.len ? ldg4(bp + p) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+            const uint32_t ev[4] = {e.x, e.y, e.z, e.w};
+            uint32_t m = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t x = ev[c] - base;
+                if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) m |= 1u << c;
+            }
+            four(m, e);
+        }
+    }
+
+    // A as a sorted array, of which only the prefix A[0..j) can meet N+(v)
+    __device__ __forceinline__ void sorted(const uint32_t *A, uint32_t j, const SetDesc &dv) {
+        const TrieView &tv = a.tv;
+        const uint32_t lane = threadIdx.x & 31;
+        if (dv.nwords || (uint64_t)dv.len > (uint64_t)a.ratio * j) {
+            // A's elements probe N+(v): its bitset, or a binary search of its uint array
+            for (uint32_t i0 = 0; i0 < j; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                const uint32_t x = i < j ? A[i] : EH_PAD;
+                one(i < j && in_set(tv, dv, x), x);
+            }
+            return;
+        }
+        // N+(v)'s elements search A[0..j)
+        const uint32_t *B = tv.nbr + dv.off;
+        for (uint32_t p0 = 0; p0 < dv.len; p0 += 32) {
+            const uint32_t p = p0 + lane;
+            const uint32_t x = p < dv.len ? __ldg(&B[p]) : EH_PAD;
+            bool hit = false;
+            if (p < dv.len) {
+                const uint32_t q = lower_bound(A, 0, j, x);
+                hit = q < j && A[q] == x;
+            }
+            one(hit, x);
+        }
+    }
+};
+
+// Level 2 of the 4-clique for z = S[r]: S[0..r) ∩ N+(z), rows (u, v, z, w).
+template <bool EMIT>
+__device__ __forceinline__ void k4_level2(const ListArgs &a, Sink &sk, const uint32_t *S, uint32_t r,
+                                          const SetDesc &dz) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (dz.len == 0 || r == 0) return;
+    if (dz.nwords || (uint64_t)dz.len > (uint64_t)a.ratio * r) {
+        for (uint32_t i0 = 0; i0 < r; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const uint32_t x = i < r ? S[i] : EH_PAD;
+            emit_one<P_K4, EMIT>(a, sk, i < r && in_set(a.tv, dz, x), x);
+        }
+        return;
+    }
+    const uint32_t *B = a.tv.nbr + dz.off;
+    for (uint32_t p0 = 0; p0 < dz.len; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        const uint32_t x = p < dz.len ? __ldg(&B[p]) : EH_PAD;
+        bool hit = false;
+        if (p < dz.len) {
+            const uint32_t q = lower_bound(S, 0, r, x);
+            hit = q < r && S[q] == x;
+        }
+        emit_one<P_K4, EMIT>(a, sk, hit, x);
+    }
+}
+
+// ------------------------------------------------------------- kernels
+
+// Heavy items: a persistent grid, one item per CTA at a time.
+template <int W, bool EMIT>
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *sA = smem;
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t s_item, s_next;
+    __shared__ unsigned long long s_cur, s_cnt;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *S = nullptr;
+    if (W == P_K4) S = smem + LA_CAP_WORDS + warp * S_CAP;
+    uint32_t *S_big = a.arena ? a.arena + (uint64_t)(blockIdx.x * LIST_WARPS + warp) * a.arena_stride : nullptr;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(a.next_item, 1u);
+            s_next = 1;
+            s_cnt = 0;
+            if (EMIT && s_item < a.n_heavy) s_cur = a.offs[s_item];
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= a.n_heavy) break;
+        const uint32_t u = a.heavy[item];
+        const SetDesc du = a.tv.desc[u];
+        StagedA st;
+        if (!stage_a(a.tv, du, a.flags, sA, &mbar, phase, st, a.status)) return;
+        Sink sk;
+        sk.n = 0;
+        sk.cur = 0;
+        sk.s_cur = &s_cur;
+        sk.end = EMIT ? a.offs[item + 1] : 0;
+        sk.key[0] = __ldg(&a.new2old[u]);
+        for (;;) {
+            uint32_t j = 0;
+            if (lane == 0) j = atomicAdd(&s_next, 1u);
+            j = __shfl_sync(FULL, j, 0);
+            if (j >= st.len) break;
+            const uint32_t v = st.mode == 0 ? __ldg(&st.Ag[j]) : st.A[j];
+            const SetDesc dv = a.tv.desc[v];
+            if (dv.len == 0) continue;
+            sk.key[1] = __ldg(&a.new2old[v]);
+            if (W == P_TRI) {
+                Level1<P_TRI, EMIT, false> l1{a, sk, nullptr, 0};
+                if (st.mode == 0) l1.bitmap(sA, st.a_lo, st.a_nw, dv);
+                else l1.sorted(st.A, j, dv);
+            } else {
+                // level 1: S = A ∩ N+(v), sorted, in the warp's buffer
+                uint32_t *Sw = min(j, dv.len) <= S_CAP ? S : S_big;
+                if (!Sw) { atomicOr(a.status, DEV_ST_RANGE); continue; }
+                Level1<P_K4, EMIT, true> l1{a, sk, Sw, 0};
+                if (st.mode == 0) l1.bitmap(sA, st.a_lo, st.a_nw, dv);
+                else l1.sorted(st.A, j, dv);
+                __syncwarp();
+                // level 2: for z in S, S_<z ∩ N+(z)
+                for (uint32_t r = 1; r < l1.ns; ++r) {
+                    const uint32_t z = Sw[r];
+                    sk.key[2] = __ldg(&a.new2old[z]);
+                    k4_level2<EMIT>(a, sk, Sw, r, a.tv.desc[z]);
+                }
+                __syncwarp();
+            }
+        }
+        if (!EMIT) {
+            const unsigned long long n = sk.n;   // warp-uniform
+            if (lane == 0 && n) atomicAdd(&s_cnt, n);
+        }
+        __syncthreads();
+        if (!EMIT && threadIdx.x == 0) a.cnt[item] = s_cnt;
+    }
+}
+
+// Light items: one warp each, A = N+(u) one element per lane (|A| <= 32).
+template <int W, bool EMIT>
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t item = blockIdx.x * LIST_WARPS + (threadIdx.x >> 5);
+    if (item >= a.n_light) return;
+    const uint32_t u = a.light[item];
+    const SetDesc du = a.tv.desc[u];
+    const uint32_t L = min(du.len, 32u);
+    const uint32_t x = lane < L ? __ldg(&a.tv.nbr[du.off + lane]) : EH_PAD;
+    SetDesc mine;
+    mine.off = 0; mine.len = 0; mine.deg = 0; mine.woff = 0; mine.lo_word = 0; mine.nwords = 0;
+    if (lane < L) mine = a.tv.desc[x];
+    Sink sk;
+    sk.n = 0;
+    sk.s_cur = nullptr;
+    sk.cur = EMIT ? a.offs[a.n_heavy + item] : 0;
+    sk.end = EMIT ? a.offs[a.n_heavy + item + 1] : 0;
+    sk.key[0] = __ldg(&a.new2old[u]);
+    for (uint32_t j = 1; j < L; ++j) {
+        const SetDesc dv = bcast_desc(mine, j);
+        if (dv.len == 0) continue;
+        const uint32_t v = __shfl_sync(FULL, x, j);
+        sk.key[1] = __ldg(&a.new2old[v]);
+        const bool h1 = lane < j && in_set(a.tv, dv, x);
+        if (W == P_TRI) {
+            emit_one<P_TRI, EMIT>(a, sk, h1, x);
+        } else {
+            const uint32_t bS = __ballot_sync(FULL, h1);   // S = A ∩ N+(v), one lane per element
+            for (uint32_t rest = bS; rest;) {
+                const uint32_t r = __ffs(rest) - 1;
+                rest &= rest - 1;
+                const SetDesc dz = bcast_desc(mine, r);
+                sk.key[2] = __ldg(&a.new2old[__shfl_sync(FULL, x, r)]);
+                const bool h2 = ((bS >> lane) & 1u) && lane < r && dz.len && in_set(a.tv, dz, x);
+                emit_one<P_K4, EMIT>(a, sk, h2, x);
+            }
+        }
+    }
+    if (!EMIT) {
+        if (lane == 0) a.cnt[a.n_heavy + item] = sk.n;
+    }
+}
+
+template <int W, bool EMIT>
+eh_status launch_pass(const ListArgs &a, uint32_t heavy_grid, cudaStream_t s) {
+    const uint32_t smem = LA_CAP_WORDS * 4 + (W == P_K4 ? LIST_WARPS * S_CAP * 4 : 0);
+    EH_CUDA_TRY(cudaFuncSetAttribute(k_list_heavy<W, EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (a.n_heavy) k_list_heavy<W, EMIT><<<heavy_grid, LIST_WARPS * 32, smem, s>>>(a);
+    if (a.n_light) k_list_light<W, EMIT><<<ceil_div_u32(a.n_light, LIST_WARPS), LIST_WARPS * 32, 0, s>>>(a);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
+}
+
+template <int W>
+eh_status heavy_grid_size(uint32_t n_heavy, uint32_t *grid) {
+    const uint32_t smem = LA_CAP_WORDS * 4 + (W == P_K4 ? LIST_WARPS * S_CAP * 4 : 0);
+    EH_CUDA_TRY(cudaFuncSetAttribute(k_list_heavy<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list_heavy<W, false>, LIST_WARPS * 32, smem));
+    const uint64_t g = (uint64_t)std::max(per_sm, 1) * eh_num_sms();
+    *grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(g, n_heavy));
+    return EH_OK;
+}
+
+struct ListBuffers {
+    unsigned long long *cnt = nullptr, *offs = nullptr;
+    unsigned int *next = nullptr;
+    uint32_t *arena = nullptr;
+    cudaStream_t s = nullptr;
+    ~ListBuffers() {
+        dev_free(cnt, s);
+        dev_free(offs, s);
+        dev_free(next, s);
+        dev_free(arena, s);
+        cudaStreamSynchronize(s);
+    }
+};
+
+template <int W>
+eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t *d_out, uint64_t capacity,
+                   uint64_t *out_n) {
+    NvtxRange nv("eh_list");
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
+    const uint64_t n_items = (uint64_t)plan->n_heavy + plan->n_light;
+    ListBuffers b;
+    b.s = s;
+    EH_TRY(dev_alloc(&b.cnt, n_items + 1, s));
+    EH_TRY(dev_alloc(&b.offs, n_items + 1, s));
+    EH_TRY(dev_alloc(&b.next, 2, s));
+    EH_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, (n_items + 1) * 8, s));
+    EH_CUDA_TRY(cudaMemsetAsync(b.next, 0, 8, s));
+    uint32_t grid = 1;
+    EH_TRY(heavy_grid_size<W>(plan->n_heavy, &grid));
+    ListArgs a;
+    a.tv = t->view();
+    a.new2old = t->d_new2old;
+    a.heavy = plan->d_heavy;
+    a.n_heavy = plan->n_heavy;
+    a.light = plan->d_light;
+    a.n_light = plan->n_light;
+    a.ratio = xo.gallop_ratio;
+    a.flags = xo.flags;
+    a.arena_stride = 0;
+    a.arena = nullptr;
+    if (W == P_K4 && t->max_out > S_CAP && plan->n_heavy) {
+        a.arena_stride = (t->max_out + 3) & ~3u;
+        EH_TRY(dev_alloc(&b.arena, (uint64_t)grid * LIST_WARPS * a.arena_stride, s));
+        a.arena = b.arena;
+    }
+    a.status = t->d_status;
+    a.out = d_out;
+    a.cap = capacity;
+    // pass 1: rows per item
+    a.next_item = b.next;
+    a.cnt = b.cnt;
+    a.offs = nullptr;
+    EH_TRY((launch_pass<W, false>(a, grid, s)));
+    uint64_t total = 0;
+    EH_TRY(dev_exclusive_scan_u64(reinterpret_cast<const uint64_t *>(b.cnt), reinterpret_cast<uint64_t *>(b.offs),
+                                  n_items + 1, s, &total));
+    EH_TRY(eh_check_status(t, s));
+    *out_n = total;
+    if (!d_out) return EH_OK;
+    if (total > capacity) {
+        eh_set_error("eh_list: the result has %llu rows, the buffer holds %llu", (unsigned long long)total,
+                     (unsigned long long)capacity);
+        return EH_ECAPACITY;
+    }
+    // pass 2: rows written into each item's range
+    a.next_item = b.next + 1;
+    a.offs = b.offs;
+    EH_TRY((launch_pass<W, true>(a, grid, s)));
+    return eh_check_status(t, s);
+}
+
+}  // namespace
+
+extern "C" eh_status eh_list(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
+                             uint32_t *d_out, uint64_t capacity, uint64_t *out_n) {
+    if (!trie || !out_n) { eh_set_error("eh_list: NULL argument"); return EH_EINVAL; }
+    if (pattern != EH_TRIANGLE && pattern != EH_CLIQUE4) {
+        eh_set_error("eh_list: only EH_TRIANGLE and EH_CLIQUE4 have rows to list");
+        return EH_EINVAL;
+    }
+    if (!d_out && capacity) { eh_set_error("eh_list: NULL buffer with a non-zero capacity"); return EH_EINVAL; }
+    const uintptr_t align = pattern == EH_CLIQUE4 ? 16 : 4;
+    if ((uintptr_t)d_out % align) {
+        eh_set_error("eh_list: the buffer must be %u-byte aligned", (unsigned)align);
+        return EH_EINVAL;
+    }
+    *out_n = 0;
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    cudaStream_t s = (cudaStream_t)stream;
+    const eh_exec_opts xo = eh_exec_defaults(xopts);
+    std::lock_guard<std::mutex> g(t->call_mu);
+    return pattern == EH_TRIANGLE ? run_list<P_TRI>(t, xo, s, d_out, capacity, out_n)
+                                  : run_list<P_K4>(t, xo, s, d_out, capacity, out_n);
+}

@@ -14,7 +14,7 @@ _lib = None
 
 PATTERNS = {"triangle": 0, "clique4": 1, "lollipop": 2, "lollipop_distinct": 3, "barbell": 4}
 STATUS = {0: "EH_OK", 1: "EH_EINVAL", 2: "EH_ENOMEM", 3: "EH_ECUDA", 4: "EH_ETIMEOUT", 5: "EH_EOVERFLOW",
-          6: "EH_EBUSY"}
+          6: "EH_EBUSY", 7: "EH_ECAPACITY"}
 EH_BUILD_DEVICE_INPUT = 1
 
 
@@ -99,6 +99,8 @@ def lib():
     L.eh_count_status.argtypes = [vp, vp]
     L.eh_count_info_get.restype = st
     L.eh_count_info_get.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, ctypes.POINTER(CountInfo)]
+    L.eh_list.restype = st
+    L.eh_list.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, vp, u64, u64p]
     L.eh_vertex_triangles.restype = st
     L.eh_vertex_triangles.argtypes = [vp, vp, u64p]
     L.eh_count_batch.restype = st
@@ -175,8 +177,12 @@ def build_opts(tau=32, min_bitset_len=0, flags=0):
     return BuildOpts(tau & 0xFFFFFFFF, min_bitset_len, flags)
 
 
-def exec_opts(gallop_ratio=0, light_max=0, cta_warps=0):
-    return ExecOpts(gallop_ratio, light_max, cta_warps, 0)
+EH_EXEC_SORTED_A = 1
+EH_EXEC_GLOBAL_A = 2
+
+
+def exec_opts(gallop_ratio=0, light_max=0, cta_warps=0, flags=0):
+    return ExecOpts(gallop_ratio, light_max, cta_warps, flags)
 
 
 def _pattern(p):
@@ -245,6 +251,27 @@ class Trie:
         s = TrieStats()
         _check(lib().eh_trie_stats_get(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in TrieStats._fields_ if f != "reserved"}
+
+    def list_into(self, pattern, d_out_ptr, capacity, xopts=None, stream=None):
+        """eh_list into a caller's device buffer of `capacity` rows; returns the
+        number of rows of the result (EHError EH_ECAPACITY if they do not fit)."""
+        n = ctypes.c_uint64(0)
+        xo = ctypes.byref(xopts) if xopts is not None else None
+        _check(lib().eh_list(self._h, _pattern(pattern), xo, _stream(stream),
+                             ctypes.c_void_p(d_out_ptr) if d_out_ptr else None, capacity, ctypes.byref(n)))
+        return int(n.value)
+
+    def list(self, pattern="triangle", xopts=None, stream=None):
+        """Every triangle ('triangle') or 4-clique ('clique4') once, as a device
+        tensor [rows, 3|4] of int32 holding the uint32 original ids in ascending
+        order (rows in no particular order).  The buffer is sized by a count."""
+        import torch
+        width = {"triangle": 3, "clique4": 4}[pattern]
+        rows = self.count(pattern, xopts=xopts, stream=stream)
+        out = torch.empty((max(rows, 1), width), dtype=torch.int32, device="cuda")
+        got = self.list_into(pattern, out.data_ptr(), rows, xopts=xopts, stream=stream)
+        assert got == rows
+        return out[:rows]
 
     def vertex_triangles(self, stream=None):
         out = np.zeros(self.n, np.uint64)

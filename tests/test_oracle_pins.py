@@ -325,3 +325,18 @@ def test_listing_loop_order_and_capacity():
     k = oracle.lib().oracle_list_triangles(g._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), 2)
     assert k == 20
     assert _rows(buf[:2]) == _rows(rows[:2]) and (buf[2:] == 7).all()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_listing_at_vertex(seed):
+    rng = np.random.default_rng(800 + seed)
+    n = int(rng.integers(6, 24))
+    e = G.random_graph(n, 0.5, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    bf = G.bf_list(A, 3)
+    t = G.bf_vertex_triangles(A)
+    for x in range(n):
+        rows = g.list_triangles_at(x)
+        assert len(rows) == t[x]
+        assert sorted(_rows(rows)) == [q for q in bf if x in q]

@@ -6,8 +6,8 @@
 // output row, the caller's ids of the clique in ascending order.
 //
 // Work items are those of the count plan: a vertex u with |N+(u)| above the
-// light bound is taken by a CTA, which stages A = N+(u) on chip (a bitmap
-// when its value range fits, else the sorted array) and whose warps take the
+// light bound is taken by a CTA, which stages A = N+(u) in shared memory (a
+// bitmap when its value range fits, else the sorted array) and whose warps take the
 // v in A dynamically; a lighter u is taken by one warp holding A one element
 // per lane.  Two passes run the same traversal.  The first stores each item's
 // number of rows, an exclusive scan turns those into output ranges, and the
@@ -16,12 +16,15 @@
 // shared-memory cursor: the output is dense, needs no global atomics, and the
 // rows of an item fill exactly the range the first pass gave it.
 //
-// Per pair the intersection picks its algorithm from the layouts as the count
-// path does (Sec. 4.2): bitset ∩ bitset by word AND; uint ∩ bitset by bit
-// probes; uint ∩ uint by binary searches from the smaller side (the side whose
-// elements the lanes hold).  Every loop over a set runs in warp-uniform rounds
+// Per pair the intersection works on what the lanes can enumerate (Sec. 4.2's
+// operations): with A as an on-chip bitmap every element of N+(v) probes one
+// bit of it; with A as a sorted array its elements probe N+(v)'s stored bitset
+// or binary-search its uint array, or N+(v)'s elements binary-search A,
+// whichever side is smaller.  Every loop over a set runs in warp-uniform rounds
 // of 32 lanes so that the matches of a round can be ranked by one ballot or
-// one warp prefix sum.
+// one warp prefix sum.  Staging uses plain loads (no bulk copy) and bitset
+// pairs go through the uint array of N+(v): the rows, not the reads, bound
+// this path.
 #include "eh_internal.cuh"
 #include "dev_util.cuh"
 
@@ -48,6 +51,7 @@ struct ListArgs {
     uint32_t arena_stride;                 // words per warp slot of the arena (4-clique, large S)
     uint32_t flags;                        // EH_EXEC_SORTED_A / EH_EXEC_GLOBAL_A
     unsigned int *next_item;               // heavy items taken so far
+    unsigned long long *cursor;            // write pass: next row of each heavy CTA's current item
     unsigned long long *cnt;               // count pass: rows per item (heavy items, then light)
     const unsigned long long *offs;        // write pass: first row of each item (n_items + 1 entries)
     uint32_t *out;                         // rows of width 3 or 4
@@ -60,7 +64,7 @@ struct ListArgs {
 struct Sink {
     unsigned long long n;        // count pass: rows found by this warp
     unsigned long long cur;      // write pass, light item: next row of the warp
-    unsigned long long *s_cur;   // write pass, heavy item: the CTA's cursor (shared memory); null if light
+    unsigned long long *s_cur;   // write pass, heavy item: the CTA's cursor (device memory); null if light
     unsigned long long end;      // write pass: end of the item's range
     uint32_t key[3];             // caller ids of the bound prefix: u, v (and z)
 };
@@ -89,7 +93,8 @@ __device__ __forceinline__ void put_row(const ListArgs &a, const Sink &sk, unsig
     }
 }
 
-// first output row of a round whose matches total `total` (warp-uniform)
+// first output row of a round whose matches total `total` (warp-uniform);
+// a heavy item's warps share its CTA's cursor, a light item's warp keeps its own
 template <bool EMIT>
 __device__ __forceinline__ unsigned long long reserve(Sink &sk, uint32_t total) {
     if (!EMIT) {
@@ -120,6 +125,12 @@ __device__ __forceinline__ void emit_one(const ListArgs &a, Sink &sk, bool hit, 
     }
 }
 
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL, x, d);
+    return x;
+}
+
 // exclusive warp prefix sum of x; total in *total
 __device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t &total) {
     const int lane = threadIdx.x & 31;
@@ -138,7 +149,7 @@ template <int W, bool EMIT>
 __device__ __forceinline__ void emit_four(const ListArgs &a, Sink &sk, uint32_t m, const uint4 &v) {
     const uint32_t k = __popc(m);
     if (!EMIT) {
-        sk.n += __reduce_add_sync(FULL, k);
+        sk.n += warp_sum(k);
         return;
     }
     uint32_t total;
@@ -149,30 +160,6 @@ __device__ __forceinline__ void emit_four(const ListArgs &a, Sink &sk, uint32_t 
 #pragma unroll
     for (int c = 0; c < 4; ++c)
         if ((m >> c) & 1u) put_row<W>(a, sk, base + r + i++, vv[c]);
-}
-
-// One round where each lane has four words of matches, x[c] standing for the values 32*(w0+c)+bit.
-template <int W, bool EMIT>
-__device__ __forceinline__ void emit_words(const ListArgs &a, Sink &sk, const uint4 &x, uint32_t w0) {
-    const uint32_t k = __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
-    if (!EMIT) {
-        sk.n += __reduce_add_sync(FULL, k);
-        return;
-    }
-    uint32_t total;
-    const uint32_t r = warp_excl(k, total);
-    const unsigned long long base = reserve<EMIT>(sk, total);
-    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-    uint32_t i = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        uint32_t b = xs[c];
-        while (b) {
-            const uint32_t bit = __ffs(b) - 1;
-            b &= b - 1;
-            put_row<W>(a, sk, base + r + i++, (w0 + c) * 32 + bit);
-        }
-    }
 }
 
 // x in the set with descriptor d (bit probe of its bitset, else binary search of its uint array)
@@ -207,31 +194,18 @@ struct StagedA {
     const uint32_t *A;    // sorted elements (modes 1, 2)
 };
 
-// Stages A = N+(u) for the CTA.  Returns false when the bounded wait for the
-// bulk copy ran out (every thread of the CTA gets false and must leave).
-__device__ bool stage_a(const TrieView &tv, const SetDesc &du, uint32_t flags, uint32_t *sA, uint64_t *mbar,
-                        uint32_t &phase, StagedA &st, uint32_t *status) {
+// Stages A = N+(u) for the CTA with plain loads: an on-chip bitmap of its
+// value range when that fits, else the sorted array when it fits, else A is
+// read from device memory.
+__device__ __forceinline__ void stage_a(const TrieView &tv, const SetDesc &du, uint32_t flags, uint32_t *sA,
+                                        StagedA &st) {
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     st.len = du.len;
     st.Ag = tv.nbr + du.off;
     const uint32_t first = __ldg(&st.Ag[0]), last = __ldg(&st.Ag[st.len - 1]);
     st.a_lo = (first >> 7) << 2;
     st.a_nw = (((last >> 5) + 1 - st.a_lo) + 3) & ~3u;
-    bool copy = false;
-    const bool bitmap_ok = !(flags & (EH_EXEC_SORTED_A | EH_EXEC_GLOBAL_A));
-    if (flags & EH_EXEC_GLOBAL_A) {
-        st.mode = 2;
-    } else if (bitmap_ok && du.nwords && du.nwords <= LA_CAP_WORDS) {   // the stored bitset, copied as is
-        st.mode = 0;
-        st.a_lo = du.lo_word;
-        st.a_nw = du.nwords;
-        copy = true;
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(mbar, st.a_nw * 4);
-            bulk_g2s(sA, tv.words + du.woff, st.a_nw * 4, mbar);
-        }
-    } else if (bitmap_ok && st.a_nw <= LA_CAP_WORDS) {   // uint array re-encoded as a bitmap on chip
+    if (!(flags & (EH_EXEC_SORTED_A | EH_EXEC_GLOBAL_A)) && st.a_nw <= LA_CAP_WORDS) {
         st.mode = 0;
         for (uint32_t i = tid * 4; i < st.a_nw; i += nthr * 4)
             *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
@@ -240,31 +214,14 @@ __device__ bool stage_a(const TrieView &tv, const SetDesc &du, uint32_t flags, u
             const uint32_t x = __ldg(&st.Ag[i]);
             atomicOr(&sA[(x >> 5) - st.a_lo], 1u << (x & 31));
         }
-    } else if (st.len <= LA_CAP_WORDS) {            // sorted array copied on chip
+    } else if (!(flags & EH_EXEC_GLOBAL_A) && st.len <= LA_CAP_WORDS) {
         st.mode = 1;
-        copy = true;
-        if (tid == 0) {
-            const uint32_t bytes = ((st.len + 3) & ~3u) * 4;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(mbar, bytes);
-            bulk_g2s(sA, st.Ag, bytes, mbar);
-        }
+        for (uint32_t i = tid; i < st.len; i += nthr) sA[i] = __ldg(&st.Ag[i]);
     } else {
         st.mode = 2;
     }
-    if (copy) {
-        const bool ok = mbar_wait(mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(status, DEV_ST_TIMEOUT);
-            mbar_wait(mbar, phase ^ 1);   // drain the copy still in flight, bounded
-            return false;
-        }
-    } else {
-        __syncthreads();
-    }
+    __syncthreads();
     st.A = st.mode == 2 ? st.Ag : sA;
-    return true;
 }
 
 // ------------------------------------------------- level-1 intersections
@@ -304,50 +261,11 @@ struct Level1 {
             emit_four<W, EMIT>(a, sk, m, v);
         }
     }
-    __device__ __forceinline__ void words(const uint4 &x, uint32_t w0) {
-        if (COLLECT) {
-            uint32_t total;
-            const uint32_t r = warp_excl(__popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w), total);
-            const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-            uint32_t i = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t b = xs[c];
-                while (b) {
-                    const uint32_t bit = __ffs(b) - 1;
-                    b &= b - 1;
-                    S[ns + r + i++] = (w0 + c) * 32 + bit;
-                }
-            }
-            ns += total;
-        } else {
-            emit_words<W, EMIT>(a, sk, x, w0);
-        }
-    }
-
-    // A as the on-chip bitmap of words [a_lo, a_lo + a_nw)
+    // A as the on-chip bitmap of words [a_lo, a_lo + a_nw): every element of
+    // N+(v) probes it (B's uint array; the padding EH_PAD is out of range)
     __device__ __forceinline__ void bitmap(const uint32_t *sA, uint32_t a_lo, uint32_t a_nw, const SetDesc &dv) {
         const TrieView &tv = a.tv;
         const uint32_t lane = threadIdx.x & 31;
-        if (dv.nwords) {
-            const uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
-            if (hi <= lo) return;   // disjoint value ranges
-            if (hi - lo <= dv.len) {   // fewer overlapping words than elements: bitset ∩ bitset
-                const uint32_t *bw = tv.words + dv.woff - dv.lo_word;
-                for (uint32_t i0 = lo; i0 < hi; i0 += 128) {
-                    const uint32_t i = i0 + lane * 4;
-                    uint4 x = make_uint4(0, 0, 0, 0);
-                    if (i < hi) {
-                        const uint4 b = ldg4(bw + i);
-                        const uint4 av = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
-                        x = make_uint4(av.x & b.x, av.y & b.y, av.z & b.z, av.w & b.w);
-                    }
-                    words(x, i);
-                }
-                return;
-            }
-        }
-        // uint N+(v): every element probes A's bitmap (the padding EH_PAD is out of range)
         const uint32_t *bp = tv.nbr + dv.off;
         const uint32_t base = a_lo * 32, nbits = a_nw * 32;
         for (uint32_t p0 = 0; p0 < dv.len; p0 += 128) {
@@ -426,22 +344,17 @@ template <int W, bool EMIT>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sA = smem;
-    __shared__ uint64_t mbar;
     __shared__ uint32_t s_item, s_next;
-    __shared__ unsigned long long s_cur, s_cnt;
+    __shared__ unsigned long long s_wcnt[LIST_WARPS];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *S = nullptr;
     if (W == P_K4) S = smem + LA_CAP_WORDS + warp * S_CAP;
     uint32_t *S_big = a.arena ? a.arena + (uint64_t)(blockIdx.x * LIST_WARPS + warp) * a.arena_stride : nullptr;
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
-    __syncthreads();
-    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(a.next_item, 1u);
             s_next = 1;
-            s_cnt = 0;
-            if (EMIT && s_item < a.n_heavy) s_cur = a.offs[s_item];
+            if (EMIT && s_item < a.n_heavy) atomicExch(a.cursor + blockIdx.x, a.offs[s_item]);
         }
         __syncthreads();
         const uint32_t item = s_item;
@@ -449,11 +362,11 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
         const uint32_t u = a.heavy[item];
         const SetDesc du = a.tv.desc[u];
         StagedA st;
-        if (!stage_a(a.tv, du, a.flags, sA, &mbar, phase, st, a.status)) return;
+        stage_a(a.tv, du, a.flags, sA, st);
         Sink sk;
         sk.n = 0;
         sk.cur = 0;
-        sk.s_cur = &s_cur;
+        sk.s_cur = EMIT ? a.cursor + blockIdx.x : nullptr;
         sk.end = EMIT ? a.offs[item + 1] : 0;
         sk.key[0] = __ldg(&a.new2old[u]);
         for (;;) {
@@ -486,12 +399,13 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
                 __syncwarp();
             }
         }
-        if (!EMIT) {
-            const unsigned long long n = sk.n;   // warp-uniform
-            if (lane == 0 && n) atomicAdd(&s_cnt, n);
-        }
+        if (!EMIT && lane == 0) s_wcnt[warp] = sk.n;   // warp-uniform
         __syncthreads();
-        if (!EMIT && threadIdx.x == 0) a.cnt[item] = s_cnt;
+        if (!EMIT && threadIdx.x == 0) {
+            unsigned long long c = 0;
+            for (uint32_t w = 0; w < LIST_WARPS; ++w) c += s_wcnt[w];
+            a.cnt[item] = c;
+        }
     }
 }
 
@@ -544,6 +458,7 @@ eh_status launch_pass(const ListArgs &a, uint32_t heavy_grid, cudaStream_t s) {
     const uint32_t smem = LA_CAP_WORDS * 4 + (W == P_K4 ? LIST_WARPS * S_CAP * 4 : 0);
     EH_CUDA_TRY(cudaFuncSetAttribute(k_list_heavy<W, EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     if (a.n_heavy) k_list_heavy<W, EMIT><<<heavy_grid, LIST_WARPS * 32, smem, s>>>(a);
+    EH_CUDA_TRY(cudaGetLastError());
     if (a.n_light) k_list_light<W, EMIT><<<ceil_div_u32(a.n_light, LIST_WARPS), LIST_WARPS * 32, 0, s>>>(a);
     EH_CUDA_TRY(cudaGetLastError());
     return EH_OK;
@@ -563,12 +478,14 @@ eh_status heavy_grid_size(uint32_t n_heavy, uint32_t *grid) {
 struct ListBuffers {
     unsigned long long *cnt = nullptr, *offs = nullptr;
     unsigned int *next = nullptr;
+    unsigned long long *cursor = nullptr;
     uint32_t *arena = nullptr;
     cudaStream_t s = nullptr;
     ~ListBuffers() {
         dev_free(cnt, s);
         dev_free(offs, s);
         dev_free(next, s);
+        dev_free(cursor, s);
         dev_free(arena, s);
         cudaStreamSynchronize(s);
     }
@@ -590,6 +507,7 @@ eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t 
     EH_CUDA_TRY(cudaMemsetAsync(b.next, 0, 8, s));
     uint32_t grid = 1;
     EH_TRY(heavy_grid_size<W>(plan->n_heavy, &grid));
+    EH_TRY(dev_alloc(&b.cursor, grid, s));
     ListArgs a;
     a.tv = t->view();
     a.new2old = t->d_new2old;
@@ -607,6 +525,7 @@ eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t 
         a.arena = b.arena;
     }
     a.status = t->d_status;
+    a.cursor = b.cursor;
     a.out = d_out;
     a.cap = capacity;
     // pass 1: rows per item

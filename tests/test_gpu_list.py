@@ -196,11 +196,11 @@ def assert_unique_triangles(rows, bits):
     import torch
     low = 64 - 2 * bits
     for part in range(1 << max(0, bits - low)):
-        sel = (rows[:, 2].to(torch.int64) >> low) == part
-        r = rows[sel]
-        key = (r[:, 0].to(torch.int64) << (bits + low)) | (r[:, 1].to(torch.int64) << low) | \
-            (r[:, 2].to(torch.int64) & ((1 << low) - 1))
-        del r, sel
+        r = rows[(rows[:, 2].to(torch.int64) >> low) == part]
+        key = r[:, 0].to(torch.int64) << (bits + low)
+        key |= r[:, 1].to(torch.int64) << low
+        key |= r[:, 2].to(torch.int64) & ((1 << low) - 1)
+        del r
         key = torch.sort(key).values
         assert not bool((key[1:] == key[:-1]).any())
         del key

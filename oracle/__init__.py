@@ -65,6 +65,8 @@ def lib():
         L.oracle_layout_is_bitset.restype = ctypes.c_int
         L.oracle_layout_is_bitset.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32]
         L.oracle_degree_order.argtypes = [vp, u32p]
+        L.oracle_vertex_order.restype = ctypes.c_int
+        L.oracle_vertex_order.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, u32p]
         _lib = L
     return _lib
 
@@ -202,6 +204,16 @@ class Graph:
         if not h:
             raise ValueError("subset id >= n")
         return Graph(0, _handle=h)
+
+    ORDERINGS = {"degree": 0, "rev_degree": 1, "random": 2, "bfs": 3, "strong_runs": 4, "shingle": 5,
+                 "hybrid": 6, "identity": 7}
+
+    def vertex_order(self, ordering, seed=0):
+        """new_to_old permutation of a node ordering (App. "Node Ordering")."""
+        out = np.empty(self.n, np.uint32)
+        if lib().oracle_vertex_order(self._h, self.ORDERINGS[ordering], seed, _u32p(out)) != 0:
+            raise ValueError("oracle_vertex_order")
+        return out
 
     def degree_order(self):
         out = np.empty(self.n, np.uint32)

@@ -559,3 +559,124 @@ void oracle_degree_order(void *h, uint32_t *new_to_old) {
     for (uint32_t i = 0; i < g->n; ++i) new_to_old[i] = t[i].id;
     free(t);
 }
+
+/* --------------------------------------------------- node orderings
+ * The dictionary orderings of App. "Node Ordering", each straight from its
+ * sequential definition.  Writes new_to_old[n] (position -> original id).
+ *   0 Degree       degree descending, ties by id
+ *   1 Rev-Degree   degree ascending, ties by id
+ *   2 Random       by the top 64-b bits of h(v), ties by id (b = bits of n)
+ *   3 BFS          FIFO breadth-first search from the first vertex of the
+ *                  Degree order, neighbours in ascending id; the vertices it
+ *                  does not reach follow in Degree order
+ *   4 Strong-Runs  for p in Degree order: label p if unlabelled, then its
+ *                  unlabelled neighbours in ascending id
+ *   5 Shingle      by the top 64-b bits of min_{w in N(v)} h(w) (all ones
+ *                  without neighbours), ties by id
+ *   6 Hybrid       the BFS order, stably re-sorted by degree descending
+ *   7 Identity
+ * h(v) is SplitMix64's output for the counter seed * 2^32 + v. */
+static uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+typedef struct { uint64_t a, b; uint32_t id; } ord_key;
+static int cmp_ord(const void *x, const void *y) {
+    const ord_key *p = (const ord_key *)x, *q = (const ord_key *)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    return p->id < q->id ? -1 : p->id > q->id;
+}
+
+static void order_by(ord_key *k, uint32_t n, uint32_t *out) {
+    qsort(k, n, sizeof(ord_key), cmp_ord);
+    for (uint32_t i = 0; i < n; ++i) out[i] = k[i].id;
+}
+
+int oracle_vertex_order(void *h, int kind, uint32_t seed, uint32_t *out) {
+    oracle_graph *g = (oracle_graph *)h;
+    const uint32_t n = g->n;
+    int b = 1;
+    while (b < 63 && (1ULL << b) < n) ++b;
+    ord_key *k = (ord_key *)malloc(sizeof(ord_key) * ((size_t)n + 1));
+    uint32_t *deg_order = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    uint32_t *label = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    if (!k || !deg_order || !label) { free(k); free(deg_order); free(label); return -1; }
+    for (uint32_t v = 0; v < n; ++v) {   /* the Degree order, used by several */
+        k[v].a = ~0ULL - (g->off[v + 1] - g->off[v]); k[v].b = 0; k[v].id = v;
+    }
+    order_by(k, n, deg_order);
+    uint32_t c = 0;
+    switch (kind) {
+    case 0:
+        memcpy(out, deg_order, sizeof(uint32_t) * n);
+        break;
+    case 1:
+        for (uint32_t v = 0; v < n; ++v) { k[v].a = g->off[v + 1] - g->off[v]; k[v].b = 0; k[v].id = v; }
+        order_by(k, n, out);
+        break;
+    case 2:
+        for (uint32_t v = 0; v < n; ++v) {
+            k[v].a = splitmix64(((uint64_t)seed << 32) | v) >> b; k[v].b = 0; k[v].id = v;
+        }
+        order_by(k, n, out);
+        break;
+    case 3:
+    case 6: {
+        for (uint32_t v = 0; v < n; ++v) label[v] = 0xFFFFFFFFu;
+        if (n) {   /* FIFO queue: out doubles as the queue */
+            uint32_t head = 0;
+            out[c] = deg_order[0]; label[deg_order[0]] = c++;
+            while (head < c) {
+                uint32_t p = out[head++];
+                for (uint64_t i = g->off[p]; i < g->off[p + 1]; ++i) {
+                    uint32_t w = g->adj[i];
+                    if (label[w] == 0xFFFFFFFFu) { label[w] = c; out[c++] = w; }
+                }
+            }
+            for (uint32_t i = 0; i < n; ++i)
+                if (label[deg_order[i]] == 0xFFFFFFFFu) { label[deg_order[i]] = c; out[c++] = deg_order[i]; }
+        }
+        if (kind == 6) {   /* stable by degree descending: ties keep their BFS position */
+            for (uint32_t v = 0; v < n; ++v) {
+                k[v].a = ~0ULL - (g->off[v + 1] - g->off[v]); k[v].b = label[v]; k[v].id = v;
+            }
+            order_by(k, n, out);
+        }
+        break;
+    }
+    case 4:
+        for (uint32_t v = 0; v < n; ++v) label[v] = 0;
+        for (uint32_t s = 0; s < n; ++s) {
+            uint32_t p = deg_order[s];
+            if (!label[p]) { label[p] = 1; out[c++] = p; }
+            for (uint64_t i = g->off[p]; i < g->off[p + 1]; ++i) {
+                uint32_t w = g->adj[i];
+                if (!label[w]) { label[w] = 1; out[c++] = w; }
+            }
+        }
+        break;
+    case 5:
+        for (uint32_t v = 0; v < n; ++v) {
+            uint64_t mn = ~0ULL;
+            for (uint64_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+                uint64_t hw = splitmix64(((uint64_t)seed << 32) | g->adj[i]);
+                if (hw < mn) mn = hw;
+            }
+            k[v].a = mn >> b; k[v].b = 0; k[v].id = v;
+        }
+        order_by(k, n, out);
+        break;
+    case 7:
+        for (uint32_t v = 0; v < n; ++v) out[v] = v;
+        break;
+    default:
+        free(k); free(deg_order); free(label);
+        return -2;
+    }
+    free(k); free(deg_order); free(label);
+    return 0;
+}

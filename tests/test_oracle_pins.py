@@ -340,3 +340,60 @@ def test_listing_at_vertex(seed):
         rows = g.list_triangles_at(x)
         assert len(rows) == t[x]
         assert sorted(_rows(rows)) == [q for q in bf if x in q]
+
+
+# ------------------------------------------------------------ node orderings
+
+# Two hubs (0 and 4) joined by the path 0-3-7-8-4; hub 0 has leaves 5, 6 and
+# hub 4 has leaves 1, 2.  The orders below were worked out by hand from the
+# definitions (App. "Node Ordering"; BFS from the highest-degree vertex,
+# neighbours in ascending id; hybrid = BFS re-sorted stably by degree).
+HUBS = [(0, 5), (0, 6), (0, 3), (3, 7), (7, 8), (8, 4), (4, 1), (4, 2)]
+HUBS_ORDERS = {
+    "degree": [0, 4, 3, 7, 8, 1, 2, 5, 6],
+    "rev_degree": [1, 2, 5, 6, 3, 7, 8, 0, 4],
+    "bfs": [0, 3, 5, 6, 7, 8, 4, 1, 2],
+    "strong_runs": [0, 3, 5, 6, 4, 1, 2, 8, 7],
+    "hybrid": [0, 4, 3, 7, 8, 5, 6, 1, 2],
+    "identity": list(range(9)),
+}
+
+
+@pytest.mark.parametrize("ordering", sorted(HUBS_ORDERS))
+def test_orderings_by_hand(ordering):
+    assert og(9, HUBS).vertex_order(ordering).tolist() == HUBS_ORDERS[ordering]
+
+
+def test_bfs_orders_unreached_vertices_by_degree():
+    # component {0..5} searched from 3 (the only degree-3 vertex); 6-7 and the
+    # isolated 8 are not reached and follow in degree order
+    e = [(0, 1), (0, 2), (1, 3), (2, 3), (3, 4), (4, 5), (6, 7)]
+    g = og(9, e)
+    assert g.vertex_order("bfs").tolist() == [3, 1, 2, 4, 0, 5, 6, 7, 8]
+    assert g.vertex_order("strong_runs").tolist() == [3, 1, 2, 4, 0, 5, 6, 7, 8]
+    assert g.vertex_order("rev_degree").tolist() == [8, 5, 6, 7, 0, 1, 2, 4, 3]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_orderings_are_permutations_and_seeded(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(20, 200))
+    g = og(n, G.random_graph(n, 0.05, rng))
+    for o in g.ORDERINGS:
+        assert sorted(g.vertex_order(o, seed).tolist()) == list(range(n)), o
+    assert g.vertex_order("random", 1).tolist() != g.vertex_order("random", 2).tolist()
+    assert g.vertex_order("random", 5).tolist() == g.vertex_order("random", 5).tolist()
+
+
+def test_shingle_puts_twins_together():
+    # vertices with equal neighbourhoods share their min-hash shingle, so they
+    # are consecutive (ties by id)
+    e = [(0, 10), (0, 11), (1, 10), (1, 11), (2, 10), (2, 11),     # 0, 1, 2 twins
+         (3, 12), (4, 12), (5, 12), (6, 13), (7, 14), (8, 15)]     # 3, 4, 5 twins
+    for seed in range(5):
+        o = og(16, e).vertex_order("shingle", seed).tolist()
+        i = o.index(0)
+        assert o[i:i + 3] == [0, 1, 2]
+        j = o.index(3)
+        assert o[j:j + 3] == [3, 4, 5]
+        assert o.index(9) == 15                     # no neighbours: last (of the ties at all ones, largest id)

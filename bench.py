@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="triangle", choices=["triangle", "clique4", "batch", "serve", "list", "all"],
+    ap.add_argument("--workload", default="triangle", choices=["triangle", "clique4", "batch", "serve", "list", "order", "all"],
                     help="triangle: the headline line; batch/serve/all add the query-batch and serving results")
     ap.add_argument("--serve-queries", type=int, default=1500)
     return ap.parse_args()
@@ -286,6 +286,62 @@ def bench_list(eh, trie, xo, alg_bytes, gold, reps=3):
             "timing": "CUDA events around eh_list (both passes, the scan and its 8-byte D2H), min of %d" % reps}
 
 
+ORDER_STUDY_GAMMAS = (1.8, 2.1, 2.5, 3.0)
+ORDER_STUDY_TAUS = (0, 32, 256)
+
+
+def bench_order(eh, n=1 << 20, n_pairs=8_000_000, reps=3):
+    """Node orderings x layout granularity on triangle counting (App. "Node
+    Ordering"; the relation- vs set-level study of Sec. 4.3): Chung-Lu graphs
+    with degree exponent gamma, tau = 0 (relation level: every set uint) and
+    set level (tau = 32, the memory-neutral default; tau = 256, the paper's).
+    Times: trie build (the ordering included) on the host clock, the count by
+    CUDA events (median of reps, L2 flushed before each)."""
+    import torch
+    import synth
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    orderings = list(eh.ORDERINGS)
+    res = {"workload": "Chung-Lu n=2^20, %d raw pairs, w_max 5e4, gamma in %s; triangle count" %
+                       (n_pairs, list(ORDER_STUDY_GAMMAS)),
+           "taus": list(ORDER_STUDY_TAUS), "graphs": {}}
+    for gi, gamma in enumerate(ORDER_STUDY_GAMMAS):
+        s, d = synth.chunglu(n, n_pairs, synth.key(1503, 120, gi), gamma=gamma)
+        rows, count0, m = {}, None, None
+        for o in orderings:
+            row = {}
+            for tau in ORDER_STUDY_TAUS:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                t = eh.Trie(s, d, n, tau=tau, ordering=o, order_seed=1)
+                torch.cuda.synchronize()
+                if tau == 0:
+                    row["build_ms"] = (time.perf_counter() - t0) * 1e3
+                    st = t.stats()
+                    m = st["n_edges"]
+                    row["max_out_degree"] = st["max_out_degree"]
+                t.count_async("triangle", out.data_ptr())
+                ms = []
+                for k in range(reps):
+                    flush.fill_(k)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    t.count_async("triangle", out.data_ptr())
+                    b.record()
+                    torch.cuda.synchronize()
+                    ms.append(a.elapsed_time(b))
+                t.status()
+                c = int(out.item())
+                if count0 is None:
+                    count0 = c
+                assert c == count0, "triangle count changed with the ordering or layout"
+                row["tri_ms_tau%d" % tau] = statistics.median(ms)
+                t.close()
+            rows[o] = row
+        res["graphs"]["gamma_%.1f" % gamma] = {"m_unique_edges": m, "triangles": count0, "orderings": rows}
+    return res
+
+
 def bench_serve(eh, n_queries=1500, tau=32, log=None):
     """Resident R-MAT-24; ego-net queries (induced edges log-uniform 100..1e6),
     patterns uniform over triangle / 4-clique / lollipop; closed-loop saturation,
@@ -495,6 +551,8 @@ def run_eh(args):
         cpu = cpu_baseline(g, args.cpu_seconds)
 
     extra = {}
+    if rank == 0 and args.workload in ("order", "all"):
+        extra["order"] = bench_order(eh)
     if rank == 0 and args.workload in ("list", "all"):
         extra["list"] = bench_list(eh, trie, xo, info["alg_bytes"], gold)
     if rank == 0 and args.workload in ("clique4", "batch", "all"):

@@ -74,7 +74,8 @@ typedef enum {
 
 typedef struct eh_trie eh_trie; /* opaque, device-resident, owned by the library */
 
-/* eh_build_trie options.  Pass NULL for the defaults (tau 32, input on host). */
+/* eh_build_trie options.  Pass NULL for the defaults (tau 32, input on host,
+ * degree ordering). */
 typedef struct {
     /* Set-level layout rule (Sec. 4.4): a set S is stored as a bitset when its
      * range max-min+1 is at most bitset_tau bits per element (range <= tau*|S|).
@@ -84,7 +85,39 @@ typedef struct {
     uint32_t bitset_tau;
     uint32_t min_bitset_len; /* sets shorter than this stay uint (default 0) */
     uint32_t flags;          /* EH_BUILD_* */
+    uint32_t ordering;       /* eh_ordering: how original ids become trie ids (default EH_ORDER_DEGREE) */
+    uint32_t order_seed;     /* seed of EH_ORDER_RANDOM and EH_ORDER_SHINGLE */
 } eh_build_opts;
+
+/* Node orderings of the dictionary encoding (App. "Node Ordering"): the
+ * permutation from original ids to the trie's ids.  Pruning keeps each edge in
+ * the set of its larger trie id, so the ordering decides the shape of N+(v)
+ * (counts do not depend on it).  Vertices without edges take part like any
+ * other.  h(v) = SplitMix64 of the counter (order_seed * 2^32 + v).
+ *   EH_ORDER_DEGREE       degree descending, ties by original id
+ *   EH_ORDER_REV_DEGREE   degree ascending, ties by original id
+ *   EH_ORDER_RANDOM       by h(v), ties by original id
+ *   EH_ORDER_BFS          breadth-first from the highest-degree vertex (first in
+ *                         EH_ORDER_DEGREE), neighbours in ascending id; vertices
+ *                         it does not reach follow in EH_ORDER_DEGREE order
+ *   EH_ORDER_STRONG_RUNS  vertices visited in EH_ORDER_DEGREE order; each
+ *                         labels itself if unlabelled, then its unlabelled
+ *                         neighbours in ascending id
+ *   EH_ORDER_SHINGLE      by the min-hash shingle min_{w in N(v)} h(w) (its top
+ *                         64 - bits(n) bits), ties by id; no neighbours: last
+ *   EH_ORDER_HYBRID       EH_ORDER_BFS positions re-sorted by degree
+ *                         descending; equal degrees keep their BFS order
+ *   EH_ORDER_IDENTITY     the original ids */
+typedef enum {
+    EH_ORDER_DEGREE = 0,
+    EH_ORDER_REV_DEGREE = 1,
+    EH_ORDER_RANDOM = 2,
+    EH_ORDER_BFS = 3,
+    EH_ORDER_STRONG_RUNS = 4,
+    EH_ORDER_SHINGLE = 5,
+    EH_ORDER_HYBRID = 6,
+    EH_ORDER_IDENTITY = 7
+} eh_ordering;
 
 #define EH_BUILD_DEVICE_INPUT 1u /* src/dst are device pointers (read on `stream`) */
 

@@ -205,6 +205,10 @@ eh_status eh_launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n
 eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint32_t *len, const uint32_t *deg,
                            uint32_t nv, uint32_t tau, uint32_t min_len, cudaStream_t s, SetDesc *desc_out,
                            uint32_t **words_out, uint64_t *n_words_out, uint64_t *n_bitset_out);
+// node ordering of the dictionary encoding: new2old[n] from the unique pairs
+// (lo << nb | hi, original ids) and the degrees (order.cu)
+eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukeys, uint64_t m, uint32_t n, int nb,
+                          const uint32_t *deg, uint32_t maxdeg, cudaStream_t s, uint32_t *new2old);
 eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
                            unsigned long long *d_out);
 eh_status eh_check_status(eh_trie *t, cudaStream_t s);

@@ -3,8 +3,8 @@
 // Steps (EmptyHeaded Sec. 2.2 and 4.4, App. A.1):
 //   1. canonical undirected pairs (lo, hi), self-loops dropped, ids checked;
 //   2. radix sort + unique: the simple edge relation (m edges);
-//   3. degrees, then new ids by (degree desc, original id asc) -- the
-//      "Degree" node ordering;
+//   3. degrees, then new ids by the chosen node ordering (order.cu; default
+//      (degree desc, original id asc), the "Degree" ordering);
 //   4. both index orders of every edge in new ids, radix sorted: the
 //      symmetric trie N(v); its prefix of smaller ids is the pruned trie N+(v)
 //      (each undirected edge kept in the set of its larger endpoint);
@@ -69,19 +69,11 @@ __global__ void k_max_u32(const uint32_t *__restrict__ x, uint64_t n, uint32_t *
     if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
 }
 
-__global__ void k_order_keys(const uint32_t *__restrict__ deg, uint32_t n, uint32_t maxdeg, int nb,
-                             uint64_t *keys) {
-    uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    keys[v] = ((uint64_t)(maxdeg - deg[v]) << nb) | v;
-}
-
-__global__ void k_relabel_maps(const uint64_t *__restrict__ keys, uint32_t n, int nb, const uint32_t *__restrict__ deg_old,
-                               uint32_t *new2old, uint32_t *old2new, uint32_t *deg_new) {
+__global__ void k_maps_from_order(const uint32_t *__restrict__ new2old, uint32_t n,
+                                  const uint32_t *__restrict__ deg_old, uint32_t *old2new, uint32_t *deg_new) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t old = (uint32_t)(keys[i] & ((1ull << nb) - 1));
-    new2old[i] = old;
+    const uint32_t old = new2old[i];
     old2new[old] = (uint32_t)i;
     deg_new[i] = deg_old[old];
 }
@@ -310,16 +302,8 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_TRY(persist_alloc(&t->d_new2old, n, &bytes));
     EH_TRY(persist_alloc(&t->d_old2new, n, &bytes));
     EH_TRY(persist_alloc(&t->d_deg, n, &bytes));
-    {
-        uint64_t *ok = nullptr, *ok2 = nullptr;
-        EH_TRY(tmp.alloc(&ok, n));
-        EH_TRY(tmp.alloc(&ok2, n));
-        if (n) k_order_keys<<<blocks_for(n), 256, 0, s>>>(deg_old, n, maxdeg, nb, ok);
-        EH_TRY(dev_radix_sort_u64(&ok, &ok2, n, nb + bits_for((uint64_t)maxdeg + 1), s));
-        if (n) k_relabel_maps<<<blocks_for(n), 256, 0, s>>>(ok, n, nb, deg_old, t->d_new2old, t->d_old2new, t->d_deg);
-        tmp.release(ok);
-        tmp.release(ok2);
-    }
+    EH_TRY(eh_vertex_order(o.ordering, o.order_seed, ukeys, m, n, nb, deg_old, maxdeg, s, t->d_new2old));
+    if (n) k_maps_from_order<<<blocks_for(n), 256, 0, s>>>(t->d_new2old, n, deg_old, t->d_old2new, t->d_deg);
 
     // 4. both index orders in new ids; symmetric and pruned tries
     const uint64_t n2 = 2 * m;
@@ -467,7 +451,10 @@ extern "C" eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uin
     o.bitset_tau = 32;
     o.min_bitset_len = 0;
     o.flags = 0;
+    o.ordering = EH_ORDER_DEGREE;
+    o.order_seed = 0;
     if (opts) o = *opts;
+    if (o.ordering > EH_ORDER_IDENTITY) { eh_set_error("eh_build_trie: unknown ordering %u", o.ordering); return EH_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     NvtxRange nv("eh_build_trie");
     eh_trie *t = new (std::nothrow) eh_trie();

@@ -24,8 +24,13 @@ class EHError(RuntimeError):
         self.status = status
 
 
+ORDERINGS = {"degree": 0, "rev_degree": 1, "random": 2, "bfs": 3, "strong_runs": 4, "shingle": 5, "hybrid": 6,
+             "identity": 7}
+
+
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("bitset_tau", ctypes.c_uint32), ("min_bitset_len", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+    _fields_ = [("bitset_tau", ctypes.c_uint32), ("min_bitset_len", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("ordering", ctypes.c_uint32), ("order_seed", ctypes.c_uint32)]
 
 
 class ExecOpts(ctypes.Structure):
@@ -173,8 +178,9 @@ def batch_profile():
     return {f: getattr(p, f) for f, _ in BatchProfile._fields_}
 
 
-def build_opts(tau=32, min_bitset_len=0, flags=0):
-    return BuildOpts(tau & 0xFFFFFFFF, min_bitset_len, flags)
+def build_opts(tau=32, min_bitset_len=0, flags=0, ordering="degree", order_seed=0):
+    o = ORDERINGS[ordering] if isinstance(ordering, str) else int(ordering)
+    return BuildOpts(tau & 0xFFFFFFFF, min_bitset_len, flags, o, order_seed)
 
 
 EH_EXEC_SORTED_A = 1
@@ -192,7 +198,8 @@ def _pattern(p):
 class Trie:
     """Device-resident trie of a simple undirected graph (eh_build_trie)."""
 
-    def __init__(self, src, dst, n_vertices, tau=32, min_bitset_len=0, stream=None):
+    def __init__(self, src, dst, n_vertices, tau=32, min_bitset_len=0, stream=None, ordering="degree",
+                 order_seed=0):
         L = lib()
         self._h = ctypes.c_void_p(0)
         flags = 0
@@ -205,7 +212,7 @@ class Trie:
             dst = np.ascontiguousarray(dst, np.uint32)
             assert len(src) == len(dst)
             ps, pd, ne = src.ctypes.data, dst.ctypes.data, len(src)
-        o = build_opts(tau, min_bitset_len, flags)
+        o = build_opts(tau, min_bitset_len, flags, ordering, order_seed)
         _check(L.eh_build_trie(ctypes.c_void_p(ps), ctypes.c_void_p(pd), ne, n_vertices, ctypes.byref(o),
                                _stream(stream), ctypes.byref(self._h)))
         self.n = n_vertices

@@ -46,11 +46,20 @@ def test_null_arguments_rejected_without_device_work():
     assert L.eh_trie_stats_get(None, None) == 1
 
 
-def test_structs_match_header_sizes():
-    assert ctypes.sizeof(ehmod.BuildOpts) == 12
-    assert ctypes.sizeof(ehmod.ExecOpts) == 16
-    assert ctypes.sizeof(ehmod.Query) == 16
-    assert ctypes.sizeof(ehmod.TrieStats) == 72
+def test_structs_match_header_sizes(tmp_path):
+    # the sizes the C compiler gives the header's structs, against the binding's
+    import subprocess
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "eh.h"\nint main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", '
+                   'sizeof(eh_build_opts), sizeof(eh_exec_opts), sizeof(eh_query), sizeof(eh_trie_stats), '
+                   'sizeof(eh_count_info), sizeof(eh_server_stats)); return 0; }\n')
+    exe = tmp_path / "sizes"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == [ctypes.sizeof(ehmod.BuildOpts), ctypes.sizeof(ehmod.ExecOpts), ctypes.sizeof(ehmod.Query),
+                   ctypes.sizeof(ehmod.TrieStats), ctypes.sizeof(ehmod.CountInfo),
+                   ctypes.sizeof(ehmod.ServerStats)]
 
 
 def test_missing_library_fails_loudly(monkeypatch):

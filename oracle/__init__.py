@@ -65,6 +65,8 @@ def lib():
         L.oracle_layout_is_bitset.restype = ctypes.c_int
         L.oracle_layout_is_bitset.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32]
         L.oracle_degree_order.argtypes = [vp, u32p]
+        L.oracle_count_selected.restype = ctypes.c_uint64
+        L.oracle_count_selected.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ip]
         L.oracle_vertex_order.restype = ctypes.c_int
         L.oracle_vertex_order.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, u32p]
         _lib = L
@@ -171,6 +173,13 @@ class Graph:
         """pattern: 'triangle' | 'clique4' | 'lollipop' | 'lollipop_distinct' | 'barbell'."""
         return {"triangle": self.triangles, "clique4": self.clique4, "lollipop": self.lollipop,
                 "lollipop_distinct": self.lollipop_distinct, "barbell": self.barbell}[pattern](nthreads=nthreads)
+
+    def count_selected(self, pattern, node):
+        """Selection queries with attribute x bound to N(node): 'clique4' (SK4)
+        or 'barbell' (SB3,1), join semantics on the symmetric relation."""
+        o = ctypes.c_int(0)
+        k = {"clique4": 0, "barbell": 1}[pattern]
+        return self._chk(lib().oracle_count_selected(self._h, k, node, ctypes.byref(o)), o)
 
     def vertex_triangles(self, verts):
         verts = np.ascontiguousarray(verts, np.uint32)

@@ -560,6 +560,55 @@ void oracle_degree_order(void *h, uint32_t *new_to_old) {
     free(t);
 }
 
+/* ---------------------------------------------------- selection queries
+ * Sec. 5.3's selection queries on the symmetric relation, join semantics,
+ * the selected attribute bound first (a selection pushed down):
+ *   kind 0  S4Clique(x,y,z,w) :- 4Clique(x,y,z,w), P(x,node): for x in N(node),
+ *           y in N(x), z in N(x) ∩ N(y), w in N(x) ∩ N(y) ∩ N(z): +1
+ *   kind 1  SBarbell(x,y,z,x',y',z') :- triangle(x,y,z), U(x,node), V(node,x'),
+ *           triangle(x',y',z'): the triangle nodes aggregated to the ordered
+ *           (y,z) pairs at x, 2 t(x); then (sum over x in N(node) of 2 t(x))^2 */
+uint64_t oracle_count_selected(void *h, int kind, uint32_t node, int *overflow) {
+    oracle_graph *g = (oracle_graph *)h;
+    int o = 0;
+    uint64_t r = 0;
+    uint64_t nn;
+    const uint32_t *Nn = set_of(g, node, 0, &nn);
+    if (kind == 0) {
+        uint64_t dmax = 0;
+        for (uint32_t v = 0; v < g->n; ++v)
+            if (g->off[v + 1] - g->off[v] > dmax) dmax = g->off[v + 1] - g->off[v];
+        uint32_t *S = (uint32_t *)malloc(sizeof(uint32_t) * (dmax + 1));
+        if (!S) { if (overflow) *overflow = 1; return 0; }
+        for (uint64_t a = 0; a < nn; ++a) {
+            uint64_t nx;
+            const uint32_t *Nx = set_of(g, Nn[a], 0, &nx);
+            for (uint64_t b = 0; b < nx; ++b) {
+                uint64_t ny;
+                const uint32_t *Ny = set_of(g, Nx[b], 0, &ny);
+                uint64_t ns = merge_into(Nx, nx, Ny, ny, S);
+                for (uint64_t c = 0; c < ns; ++c) {
+                    uint64_t nz;
+                    const uint32_t *Nz = set_of(g, S[c], 0, &nz);
+                    if (__builtin_add_overflow(r, merge_count(S, ns, Nz, nz), &r)) o = 1;
+                }
+            }
+        }
+        free(S);
+    } else {
+        uint64_t *t = (uint64_t *)malloc(sizeof(uint64_t) * (nn + 1));
+        if (!t) { if (overflow) *overflow = 1; return 0; }
+        oracle_vertex_triangles(h, Nn, nn, t);
+        uint64_t half = 0;
+        for (uint64_t a = 0; a < nn; ++a)
+            if (__builtin_add_overflow(half, 2 * t[a], &half)) o = 1;
+        if (__builtin_mul_overflow(half, half, &r)) o = 1;
+        free(t);
+    }
+    if (overflow) *overflow = o;
+    return r;
+}
+
 /* --------------------------------------------------- node orderings
  * The dictionary orderings of App. "Node Ordering", each straight from its
  * sequential definition.  Writes new_to_old[n] (position -> original id).

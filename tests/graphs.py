@@ -144,3 +144,29 @@ def bf_barbell(A):
                     for _ in tri[x2]:
                         c += 1
     return c
+
+
+def bf_sk4(A, node):
+    """Ordered (x,y,z,w) with x in N(node) and all six pairs adjacent, by
+    enumerating every tuple."""
+    n = len(A)
+    c = 0
+    for x in range(n):
+        if not A[node, x]:
+            continue
+        for y, z, w in itertools.product(range(n), repeat=3):
+            if A[x, y] and A[x, z] and A[x, w] and A[y, z] and A[y, w] and A[z, w]:
+                c += 1
+    return c
+
+
+def bf_sbarbell(A, node):
+    """Ordered (x,y,z,x',y',z'): triangles at x and x', both x, x' in N(node)."""
+    n = len(A)
+    tri = [sum(1 for y in range(n) for z in range(n) if A[x, y] and A[y, z] and A[x, z]) for x in range(n)]
+    c = 0
+    for x in range(n):
+        for x2 in range(n):
+            if A[node, x] and A[node, x2]:
+                c += tri[x] * tri[x2]
+    return c

@@ -397,3 +397,33 @@ def test_shingle_puts_twins_together():
         j = o.index(3)
         assert o[j:j + 3] == [3, 4, 5]
         assert o.index(9) == 15                     # no neighbours: last (of the ties at all ones, largest id)
+
+
+
+# ------------------------------------------------------------ selections
+
+@pytest.mark.parametrize("seed", range(5))
+def test_selection_queries_vs_tuple_enumeration(seed):
+    rng = np.random.default_rng(1200 + seed)
+    n = int(rng.integers(5, 11))
+    e = G.random_graph(n, 0.6, rng)
+    A = G.adjacency(n, e)
+    g = og(n, e)
+    for node in range(n):
+        assert g.count_selected("clique4", node) == G.bf_sk4(A, node)
+        assert g.count_selected("barbell", node) == G.bf_sbarbell(A, node)
+        d3 = np.diag(A @ A @ A)                      # 2 t(x)
+        assert g.count_selected("barbell", node) == int(A[node] @ d3) ** 2
+
+
+def test_selection_closed_forms():
+    for n in (4, 5, 7):
+        g = og(n, G.complete(n))
+        for node in (0, n - 1):
+            assert g.count_selected("clique4", node) == (n - 1) ** 2 * (n - 2) * (n - 3)
+            assert g.count_selected("barbell", node) == (n - 1) ** 4 * (n - 2) ** 2
+    g = og(10, G.petersen())                         # triangle-free
+    assert g.count_selected("clique4", 0) == 0 and g.count_selected("barbell", 0) == 0
+    g = og(6, [(0, 1), (1, 2), (0, 2), (3, 4)])      # node 5 isolated, node 3 next to no triangle
+    assert g.count_selected("barbell", 5) == 0 and g.count_selected("barbell", 3) == 0
+    assert g.count_selected("barbell", 0) == (2 + 2) ** 2

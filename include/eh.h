@@ -257,6 +257,28 @@ eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint64_t *out_t
 eh_status eh_list(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
                   uint32_t *d_out, uint64_t capacity, uint64_t *out_n);
 
+/* Selection queries (Sec. 5.3): a pattern with one attribute bound to a given
+ * vertex, on the undirected relation with join semantics (ordered tuples),
+ * the selection pushed below the rest of the plan.
+ *   EH_SEL_CLIQUE4  S4Clique(x,y,z,w) :- 4Clique(x,y,z,w), P(x,node):
+ *                   sum over x in N(node) of the ordered (y,z,w) closing a
+ *                   4-clique with x = 6 x (4-cliques containing x), each x's
+ *                   4-cliques counted as the triangles of G[N(x)]
+ *   EH_SEL_BARBELL  SBarbell(x,y,z,x',y',z') :- triangle(x,y,z), U(x,node),
+ *                   V(node,x'), triangle(x',y',z'):
+ *                   (sum over x in N(node) of 2 t(x))^2                      */
+typedef enum {
+    EH_SEL_CLIQUE4 = 0,
+    EH_SEL_BARBELL = 1
+} eh_sel_pattern;
+
+/* eh_count_selected -- the count of a selection query for the selected vertex
+ * `node` (original id; EH_EINVAL if >= n_vertices).  Writes *out_count (host)
+ * and synchronises `stream`.  EH_EOVERFLOW above 2^64 - 1.  Serialised with
+ * the other synchronous counts of the trie. */
+eh_status eh_count_selected(const eh_trie *trie, eh_sel_pattern pattern, uint32_t node, const eh_exec_opts *xopts,
+                            void *stream, uint64_t *out_count);
+
 /* eh_count_batch -- n_queries independent queries in one persistent launch.
  * Each query's count goes to out_counts[i] and its status to out_status[i]
  * (a failing query does not fail the others; the call returns the first

@@ -52,6 +52,16 @@ __global__ void k_barbell(const unsigned long long *__restrict__ vt, const uint6
     }
 }
 
+// sum of t(x) over the symmetric set N(node) (one block)
+__global__ void k_sel_sum(const unsigned long long *__restrict__ vt, const uint64_t *__restrict__ soff,
+                          const uint32_t *__restrict__ snbr, const uint32_t *__restrict__ deg, uint32_t node,
+                          unsigned long long *out) {
+    unsigned long long sum = 0;
+    for (uint32_t i = threadIdx.x; i < deg[node]; i += blockDim.x) sum += vt[snbr[soff[node] + i]];
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(out, sum);
+}
+
 __global__ void k_vt_to_old(const unsigned long long *vt, const uint32_t *new2old, uint32_t n, unsigned long long *out) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[new2old[i]] = vt[i];
@@ -249,4 +259,54 @@ extern "C" eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint
     dev_free(vo, s);
     cudaStreamSynchronize(s);
     return st;
+}
+
+extern "C" eh_status eh_count_selected(const eh_trie *trie, eh_sel_pattern pattern, uint32_t node,
+                                       const eh_exec_opts *xopts, void *stream, uint64_t *out_count) {
+    if (!trie || !out_count) { eh_set_error("eh_count_selected: NULL argument"); return EH_EINVAL; }
+    if (pattern != EH_SEL_CLIQUE4 && pattern != EH_SEL_BARBELL) {
+        eh_set_error("eh_count_selected: unknown selection pattern %d", (int)pattern);
+        return EH_EINVAL;
+    }
+    if (node >= trie->n) { eh_set_error("eh_count_selected: node %u >= n_vertices %u", node, trie->n); return EH_EINVAL; }
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    cudaStream_t s = (cudaStream_t)stream;
+    const eh_exec_opts xo = eh_exec_defaults(xopts);
+    std::lock_guard<std::mutex> g(t->call_mu);
+    uint32_t node_new = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&node_new, t->d_old2new + node, 4, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (pattern == EH_SEL_CLIQUE4) {
+        uint64_t k = 0;
+        EH_TRY(eh_sk4_total(t, node_new, xo, s, &k));
+        if (k > ~0ull / 6) { eh_set_error("SK4 count exceeds uint64"); return EH_EOVERFLOW; }
+        *out_count = 6 * k;
+        return EH_OK;
+    }
+    // SB3,1: per-vertex triangle counts (the triangle nodes of the GHD), then the
+    // selection node: (sum over x in N(node) of 2 t(x))^2
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
+    unsigned long long *vt = nullptr;
+    EH_TRY(dev_alloc(&vt, (uint64_t)t->n + 1, s));
+    eh_status st = EH_OK;
+    if (cudaMemsetAsync(vt, 0, ((uint64_t)t->n + 1) * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(t->d_scratch, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess)
+        st = EH_ECUDA;
+    if (st == EH_OK)
+        st = eh_launch_triangle(t, *plan, t->view(), M_VERTEX, xo, s, t->d_scratch + SC_T, t->d_scratch + SC_CNT,
+                                t->d_status, vt, nullptr);
+    unsigned long long sum = 0;
+    if (st == EH_OK) {
+        k_sel_sum<<<1, 1024, 0, s>>>(vt, t->d_soff, t->d_snbr, t->d_deg, node_new, vt + t->n);
+        if (cudaMemcpyAsync(&sum, vt + t->n, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) st = EH_ECUDA;
+    }
+    if (st == EH_OK) st = check_status(t, s);
+    dev_free(vt, s);
+    cudaStreamSynchronize(s);
+    EH_TRY(st);
+    const unsigned __int128 half = (unsigned __int128)2 * sum, b = half * half;
+    if ((b >> 64) != 0) { eh_set_error("SB3,1 count exceeds uint64"); return EH_EOVERFLOW; }
+    *out_count = (uint64_t)b;
+    return EH_OK;
 }

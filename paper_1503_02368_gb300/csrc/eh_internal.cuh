@@ -209,6 +209,8 @@ eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint3
 // (lo << nb | hi, original ids) and the degrees (order.cu)
 eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukeys, uint64_t m, uint32_t n, int nb,
                           const uint32_t *deg, uint32_t maxdeg, cudaStream_t s, uint32_t *new2old);
+// SK4 per-x sum over the selected vertex's neighbours (list.cu)
+eh_status eh_sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaStream_t s, uint64_t *total);
 eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
                            unsigned long long *d_out);
 eh_status eh_check_status(eh_trie *t, cudaStream_t s);

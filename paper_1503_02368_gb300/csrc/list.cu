@@ -50,6 +50,9 @@ struct ListArgs {
     uint32_t ratio;
     uint32_t arena_stride;                 // words per warp slot of the arena (4-clique, large S)
     uint32_t flags;                        // EH_EXEC_SORTED_A / EH_EXEC_GLOBAL_A
+    const uint64_t *a_off;                 // non-null: A(u) is the symmetric set N(u) (selection queries):
+    const uint32_t *a_nbr;                 //   a_nbr[a_off[u] ..] of a_len[u] ids; null: A(u) = N+(u)
+    const uint32_t *a_len;
     unsigned int *next_item;               // heavy items taken so far
     unsigned long long *cursor;            // write pass: next row of each heavy CTA's current item
     unsigned long long *cnt;               // count pass: rows per item (heavy items, then light)
@@ -197,11 +200,11 @@ struct StagedA {
 // Stages A = N+(u) for the CTA with plain loads: an on-chip bitmap of its
 // value range when that fits, else the sorted array when it fits, else A is
 // read from device memory.
-__device__ __forceinline__ void stage_a(const TrieView &tv, const SetDesc &du, uint32_t flags, uint32_t *sA,
+__device__ __forceinline__ void stage_a(const uint32_t *Ag, uint32_t len, uint32_t flags, uint32_t *sA,
                                         StagedA &st) {
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    st.len = du.len;
-    st.Ag = tv.nbr + du.off;
+    st.len = len;
+    st.Ag = Ag;
     const uint32_t first = __ldg(&st.Ag[0]), last = __ldg(&st.Ag[st.len - 1]);
     st.a_lo = (first >> 7) << 2;
     st.a_nw = (((last >> 5) + 1 - st.a_lo) + 3) & ~3u;
@@ -360,9 +363,12 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
         const uint32_t item = s_item;
         if (item >= a.n_heavy) break;
         const uint32_t u = a.heavy[item];
-        const SetDesc du = a.tv.desc[u];
         StagedA st;
-        stage_a(a.tv, du, a.flags, sA, st);
+        if (a.a_off) stage_a(a.a_nbr + a.a_off[u], a.a_len[u], a.flags, sA, st);
+        else {
+            const SetDesc du = a.tv.desc[u];
+            stage_a(a.tv.nbr + du.off, du.len, a.flags, sA, st);
+        }
         Sink sk;
         sk.n = 0;
         sk.cur = 0;
@@ -416,9 +422,9 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
     const uint32_t item = blockIdx.x * LIST_WARPS + (threadIdx.x >> 5);
     if (item >= a.n_light) return;
     const uint32_t u = a.light[item];
-    const SetDesc du = a.tv.desc[u];
-    const uint32_t L = min(du.len, 32u);
-    const uint32_t x = lane < L ? __ldg(&a.tv.nbr[du.off + lane]) : EH_PAD;
+    const uint32_t *Ag = a.a_off ? a.a_nbr + a.a_off[u] : a.tv.nbr + a.tv.desc[u].off;
+    const uint32_t L = min(a.a_off ? a.a_len[u] : a.tv.desc[u].len, 32u);
+    const uint32_t x = lane < L ? __ldg(&Ag[lane]) : EH_PAD;
     SetDesc mine;
     mine.off = 0; mine.len = 0; mine.deg = 0; mine.woff = 0; mine.lo_word = 0; mine.nwords = 0;
     if (lane < L) mine = a.tv.desc[x];
@@ -491,13 +497,25 @@ struct ListBuffers {
     }
 };
 
+// The work items of one run and where their A sets come from.
+struct Items {
+    const uint32_t *heavy = nullptr, *light = nullptr;   // device lists
+    uint32_t n_heavy = 0, n_light = 0;
+    const uint64_t *a_off = nullptr;                      // symmetric sets (selection queries); null: N+(u)
+    const uint32_t *a_nbr = nullptr, *a_len = nullptr;
+};
+
+__global__ void k_gather_u32(const uint32_t *__restrict__ idx, uint32_t n, const uint32_t *__restrict__ val,
+                             uint32_t *out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = val[idx[i]];
+}
+
+// Count pass (and, when d_out is set, the write pass) over the items.
 template <int W>
-eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t *d_out, uint64_t capacity,
-                   uint64_t *out_n) {
-    NvtxRange nv("eh_list");
-    WorkPlan *plan = nullptr;
-    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
-    const uint64_t n_items = (uint64_t)plan->n_heavy + plan->n_light;
+eh_status run_items(eh_trie *t, const Items &it, const eh_exec_opts &xo, cudaStream_t s, uint32_t *d_out,
+                    uint64_t capacity, uint64_t *out_n) {
+    const uint64_t n_items = (uint64_t)it.n_heavy + it.n_light;
     ListBuffers b;
     b.s = s;
     EH_TRY(dev_alloc(&b.cnt, n_items + 1, s));
@@ -506,20 +524,24 @@ eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t 
     EH_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, (n_items + 1) * 8, s));
     EH_CUDA_TRY(cudaMemsetAsync(b.next, 0, 8, s));
     uint32_t grid = 1;
-    EH_TRY(heavy_grid_size<W>(plan->n_heavy, &grid));
+    EH_TRY(heavy_grid_size<W>(it.n_heavy, &grid));
     EH_TRY(dev_alloc(&b.cursor, grid, s));
     ListArgs a;
     a.tv = t->view();
     a.new2old = t->d_new2old;
-    a.heavy = plan->d_heavy;
-    a.n_heavy = plan->n_heavy;
-    a.light = plan->d_light;
-    a.n_light = plan->n_light;
+    a.heavy = it.heavy;
+    a.n_heavy = it.n_heavy;
+    a.light = it.light;
+    a.n_light = it.n_light;
+    a.a_off = it.a_off;
+    a.a_nbr = it.a_nbr;
+    a.a_len = it.a_len;
     a.ratio = xo.gallop_ratio;
     a.flags = xo.flags;
     a.arena_stride = 0;
     a.arena = nullptr;
-    if (W == P_K4 && t->max_out > S_CAP && plan->n_heavy) {
+    // |S| <= |N+(v)| <= max out-degree, whatever A is
+    if (W == P_K4 && t->max_out > S_CAP && it.n_heavy) {
         a.arena_stride = (t->max_out + 3) & ~3u;
         EH_TRY(dev_alloc(&b.arena, (uint64_t)grid * LIST_WARPS * a.arena_stride, s));
         a.arena = b.arena;
@@ -551,6 +573,77 @@ eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t 
     return eh_check_status(t, s);
 }
 
+template <int W>
+eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t *d_out, uint64_t capacity,
+                   uint64_t *out_n) {
+    NvtxRange nv("eh_list");
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
+    Items it;
+    it.heavy = plan->d_heavy;
+    it.n_heavy = plan->n_heavy;
+    it.light = plan->d_light;
+    it.n_light = plan->n_light;
+    return run_items<W>(t, it, xo, s, d_out, capacity, out_n);
+}
+
+// 4-cliques through each x in N(node): the triangles of G[N(x)], counted by
+// the 4-clique passes with A = N(x) (symmetric) and y over all of A.  Items
+// are the x with d(x) >= 3 (fewer neighbours hold no triangle), split by d(x).
+eh_status sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaStream_t s, uint64_t *total) {
+    *total = 0;
+    uint64_t base = 0;
+    uint32_t dn = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&base, t->d_soff + node_new, 8, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaMemcpyAsync(&dn, t->d_deg + node_new, 4, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!dn) return EH_OK;
+    std::vector<uint32_t> xs(dn), dx(dn), heavy, light;
+    {
+        uint32_t *d_dx = nullptr;
+        EH_TRY(dev_alloc(&d_dx, dn, s));
+        k_gather_u32<<<(dn + 255) / 256, 256, 0, s>>>(t->d_snbr + base, dn, t->d_deg, d_dx);
+        cudaError_t e1 = cudaMemcpyAsync(xs.data(), t->d_snbr + base, (uint64_t)dn * 4, cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaMemcpyAsync(dx.data(), d_dx, (uint64_t)dn * 4, cudaMemcpyDeviceToHost, s);
+        cudaError_t e3 = cudaStreamSynchronize(s);
+        dev_free(d_dx, s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            eh_set_error("sk4: reading the selected vertex's neighbours failed");
+            return EH_ECUDA;
+        }
+    }
+    for (uint32_t i = 0; i < dn; ++i) {
+        if (dx[i] > xo.light_max) heavy.push_back(xs[i]);
+        else if (dx[i] >= 3) light.push_back(xs[i]);
+    }
+    uint32_t *d_items = nullptr;
+    EH_TRY(dev_alloc(&d_items, heavy.size() + light.size(), s));
+    eh_status st = EH_OK;
+    if (!heavy.empty() &&
+        cudaMemcpyAsync(d_items, heavy.data(), heavy.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = EH_ECUDA;
+    if (st == EH_OK && !light.empty() &&
+        cudaMemcpyAsync(d_items + heavy.size(), light.data(), light.size() * 4, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        st = EH_ECUDA;
+    if (st == EH_OK) {
+        Items it;
+        it.heavy = d_items;
+        it.n_heavy = (uint32_t)heavy.size();
+        it.light = d_items + heavy.size();
+        it.n_light = (uint32_t)light.size();
+        it.a_off = t->d_soff;
+        it.a_nbr = t->d_snbr;
+        it.a_len = t->d_deg;
+        st = run_items<P_K4>(t, it, xo, s, nullptr, 0, total);
+    } else {
+        eh_set_error("sk4: copying the selected items failed");
+    }
+    cudaStreamSynchronize(s);
+    dev_free(d_items, s);
+    return st;
+}
+
 }  // namespace
 
 extern "C" eh_status eh_list(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
@@ -573,4 +666,10 @@ extern "C" eh_status eh_list(const eh_trie *trie, eh_pattern pattern, const eh_e
     std::lock_guard<std::mutex> g(t->call_mu);
     return pattern == EH_TRIANGLE ? run_list<P_TRI>(t, xo, s, d_out, capacity, out_n)
                                   : run_list<P_K4>(t, xo, s, d_out, capacity, out_n);
+}
+
+// SK4 (Sec. 5.3): 6 x the 4-cliques through each neighbour x of the selected
+// vertex, summed over x (original-id lookup and overflow checks in api.cu)
+eh_status eh_sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaStream_t s, uint64_t *total) {
+    return sk4_total(t, node_new, xo, s, total);
 }

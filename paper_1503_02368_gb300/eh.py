@@ -104,6 +104,8 @@ def lib():
     L.eh_count_status.argtypes = [vp, vp]
     L.eh_count_info_get.restype = st
     L.eh_count_info_get.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, ctypes.POINTER(CountInfo)]
+    L.eh_count_selected.restype = st
+    L.eh_count_selected.argtypes = [vp, st, u32, ctypes.POINTER(ExecOpts), vp, u64p]
     L.eh_list.restype = st
     L.eh_list.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, vp, u64, u64p]
     L.eh_vertex_triangles.restype = st
@@ -258,6 +260,15 @@ class Trie:
         s = TrieStats()
         _check(lib().eh_trie_stats_get(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in TrieStats._fields_ if f != "reserved"}
+
+    def count_selected(self, pattern, node, xopts=None, stream=None):
+        """Selection query count (eh_count_selected): 'clique4' (SK4) or
+        'barbell' (SB3,1) with attribute x bound to the neighbours of `node`."""
+        out = ctypes.c_uint64(0)
+        xo = ctypes.byref(xopts) if xopts is not None else None
+        _check(lib().eh_count_selected(self._h, {"clique4": 0, "barbell": 1}[pattern], node, xo, _stream(stream),
+                                       ctypes.byref(out)))
+        return int(out.value)
 
     def list_into(self, pattern, d_out_ptr, capacity, xopts=None, stream=None):
         """eh_list into a caller's device buffer of `capacity` rows; returns the

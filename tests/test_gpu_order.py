@@ -82,3 +82,46 @@ def test_unknown_ordering_rejected(eh):
     with pytest.raises(eh.EHError) as ei:
         eh.Trie(np.array([0, 1], np.uint32), np.array([1, 2], np.uint32), 3, ordering=8)
     assert ei.value.status == 1
+
+
+# ------------------------------------------------------------ selection queries (Sec. 5.3)
+
+@pytest.mark.parametrize("seed", range(4))
+def test_selection_queries_random_graphs(eh, seed):
+    rng = np.random.default_rng(1300 + seed)
+    n = int(rng.integers(40, 300))
+    s, d = G.arrays(G.random_graph(n, float(rng.choice([0.05, 0.2, 0.4])), rng))
+    o = oracle.Graph(n, s, d)
+    for tau in (0, 32):
+        t = eh.Trie(s, d, n, tau=tau)
+        for node in rng.choice(n, 6, replace=False):
+            node = int(node)
+            for p in ("clique4", "barbell"):
+                assert t.count_selected(p, node) == o.count_selected(p, node), (p, node, tau)
+
+
+def test_selection_queries_rmat_hubs_and_knobs(eh):
+    # the top hubs as selected vertices: neighbours with hundreds of neighbours (CTA path)
+    g = W.rmat_graph(12, 1503 + 12)
+    o = oracle.Graph(g["n"], g["src"], g["dst"])
+    deg = o.degrees()
+    rank = np.argsort(-deg.astype(np.int64))
+    nodes = [int(rank[0]), int(rank[1]), int(rank[50]), int(np.argmax(deg == 5))]
+    want = {v: (o.count_selected("clique4", v), o.count_selected("barbell", v)) for v in nodes}
+    for tau in (0, 32):
+        t = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+        for node in nodes:
+            assert t.count_selected("clique4", node) == want[node][0], (node, tau)
+            assert t.count_selected("clique4", node, xopts=eh.exec_opts(light_max=8, flags=1)) == want[node][0]
+            assert t.count_selected("barbell", node) == want[node][1], node
+
+
+def test_selection_closed_forms_and_errors(eh):
+    n = 40
+    s, d = G.arrays(G.complete(n))
+    t = eh.Trie(s, d, n, tau=32)
+    assert t.count_selected("clique4", 7) == (n - 1) ** 2 * (n - 2) * (n - 3)
+    assert t.count_selected("barbell", 7) == (n - 1) ** 4 * (n - 2) ** 2
+    with pytest.raises(eh.EHError) as ei:
+        t.count_selected("clique4", n)
+    assert ei.value.status == 1

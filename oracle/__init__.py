@@ -62,6 +62,9 @@ def lib():
             f.argtypes = [vp, u32p, ctypes.c_uint64]
         L.oracle_induced.restype = vp
         L.oracle_induced.argtypes = [vp, u32p, ctypes.c_uint64]
+        L.oracle_block_layout.restype = ctypes.c_uint64
+        L.oracle_block_layout.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, u32p,
+                                          ctypes.POINTER(ctypes.c_uint8)]
         L.oracle_layout_is_bitset.restype = ctypes.c_int
         L.oracle_layout_is_bitset.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32]
         L.oracle_degree_order.argtypes = [vp, u32p]
@@ -233,3 +236,13 @@ class Graph:
 def layout_is_bitset(sorted_set, tau):
     s = np.ascontiguousarray(sorted_set, np.uint32)
     return bool(lib().oracle_layout_is_bitset(_u32p(s), len(s), tau))
+
+
+def block_layout(sorted_set, tau):
+    """Composite layout of a sorted set: (block ids, is_bitset) per 256-value block."""
+    s = np.ascontiguousarray(sorted_set, np.uint32)
+    ids = np.empty(max(len(s), 1), np.uint32)
+    kind = np.empty(max(len(s), 1), np.uint8)
+    k = int(lib().oracle_block_layout(_u32p(s), len(s), tau, _u32p(ids),
+                                      kind.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return ids[:k].copy(), kind[:k].astype(bool)

@@ -542,6 +542,26 @@ int oracle_layout_is_bitset(const uint32_t *set, uint64_t len, uint32_t tau) {
     return range <= (uint64_t)tau * len;
 }
 
+/* Composite (block-level) layout of Sec. 4.3: the value domain cut into
+ * blocks of 256 values; a block holding c values of the set is a 256-bit
+ * bitset when 256 <= tau * c (the set-level rule applied to the block's
+ * fixed range), else its values stay a uint run.  tau = 0: every block uint;
+ * tau = UINT32_MAX: every block bitset.  Writes, per block present (ascending
+ * block id = value / 256), its id and kind (1 = bitset); returns the count. */
+uint64_t oracle_block_layout(const uint32_t *set, uint64_t len, uint32_t tau, uint32_t *block_id,
+                             uint8_t *is_bitset) {
+    uint64_t nb = 0, i = 0;
+    while (i < len) {
+        uint32_t b = set[i] / 256;
+        uint64_t c = 0;
+        while (i < len && set[i] / 256 == b) { ++c; ++i; }
+        block_id[nb] = b;
+        is_bitset[nb] = tau == 0xFFFFFFFFu ? 1 : (tau != 0 && (uint64_t)tau * c >= 256);
+        ++nb;
+    }
+    return nb;
+}
+
 typedef struct { uint64_t d; uint32_t id; } deg_id;
 static int cmp_deg(const void *x, const void *y) {
     const deg_id *a = (const deg_id *)x, *b = (const deg_id *)y;

@@ -427,3 +427,33 @@ def test_selection_closed_forms():
     g = og(6, [(0, 1), (1, 2), (0, 2), (3, 4)])      # node 5 isolated, node 3 next to no triangle
     assert g.count_selected("barbell", 5) == 0 and g.count_selected("barbell", 3) == 0
     assert g.count_selected("barbell", 0) == (2 + 2) ** 2
+
+
+
+# ------------------------------------------------------------ composite layout
+
+def test_block_layout_rule():
+    # block 0 holds 1 value, block 1 holds 2, block 3 all 256
+    S = np.array([1, 300, 301] + list(range(768, 1024)), np.uint32)
+    ids, kind = oracle.block_layout(S, 32)
+    assert ids.tolist() == [0, 1, 3] and kind.tolist() == [False, False, True]
+    ids, kind = oracle.block_layout(S, 128)              # 2 * 128 >= 256 in block 1
+    assert kind.tolist() == [False, True, True]
+    assert oracle.block_layout(S, 256)[1].tolist() == [True, True, True]
+    assert oracle.block_layout(S, 0)[1].tolist() == [False, False, False]
+    assert oracle.block_layout(S, 0xFFFFFFFF)[1].tolist() == [True, True, True]
+    assert oracle.block_layout(S, 1)[1].tolist() == [False, False, True]   # only a full block at tau 1
+    assert oracle.block_layout(np.zeros(0, np.uint32), 32)[0].tolist() == []
+
+
+def test_block_layout_vs_per_block_set_rule():
+    # each block's kind is the set-level rule applied to the block's values with range 256
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        S = np.unique(rng.integers(0, 5000, size=int(rng.integers(1, 600)))).astype(np.uint32)
+        tau = int(rng.choice([1, 8, 32, 100, 256]))
+        ids, kind = oracle.block_layout(S, tau)
+        assert ids.tolist() == sorted(set((S // 256).tolist()))
+        for b, k in zip(ids, kind):
+            c = int(((S // 256) == b).sum())
+            assert k == (256 <= tau * c)

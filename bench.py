@@ -293,8 +293,9 @@ ORDER_STUDY_TAUS = (0, 32, 256)
 def bench_order(eh, n=1 << 20, n_pairs=8_000_000, reps=3):
     """Node orderings x layout granularity on triangle counting (App. "Node
     Ordering"; the relation- vs set-level study of Sec. 4.3): Chung-Lu graphs
-    with degree exponent gamma, tau = 0 (relation level: every set uint) and
-    set level (tau = 32, the memory-neutral default; tau = 256, the paper's).
+    with degree exponent gamma, tau = 0 (relation level: every set uint),
+    set level (tau = 32, the memory-neutral default; tau = 256, the paper's)
+    and block level (256-value blocks, tau = 256).
     Times: trie build (the ordering included) on the host clock, the count by
     CUDA events (median of reps, L2 flushed before each)."""
     import torch
@@ -337,6 +338,22 @@ def bench_order(eh, n=1 << 20, n_pairs=8_000_000, reps=3):
                 assert c == count0, "triangle count changed with the ordering or layout"
                 row["tri_ms_tau%d" % tau] = statistics.median(ms)
                 t.close()
+            # block level: 256-value blocks, bitset when 256 <= tau * count (tau = 256)
+            t = eh.Trie(s, d, n, tau=256, ordering=o, order_seed=1, block_layout=True)
+            t.count_async("triangle", out.data_ptr())
+            ms = []
+            for k in range(reps):
+                flush.fill_(k)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                t.count_async("triangle", out.data_ptr())
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t.status()
+            assert int(out.item()) == count0, "triangle count changed with the block layout"
+            row["tri_ms_block256"] = statistics.median(ms)
+            t.close()
             rows[o] = row
         res["graphs"]["gamma_%.1f" % gamma] = {"m_unique_edges": m, "triangles": count0, "orderings": rows}
     return res

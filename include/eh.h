@@ -120,6 +120,12 @@ typedef enum {
 } eh_ordering;
 
 #define EH_BUILD_DEVICE_INPUT 1u /* src/dst are device pointers (read on `stream`) */
+/* Composite (block-level) layout of Sec. 4.3 instead of the set-level one: the
+ * value domain cut into blocks of 256 values; in each pruned set a block
+ * holding c values is a 256-bit bitset when 256 <= bitset_tau * c, else its
+ * run of the uint array.  Triangle counts of such a trie intersect block
+ * directories (eh_trie_export_blocks); the other patterns use the uint arrays. */
+#define EH_BUILD_BLOCK_LAYOUT 2u
 
 /* Execution knobs for the intersection kernels.  NULL = defaults. */
 typedef struct {
@@ -278,6 +284,19 @@ typedef enum {
  * the other synchronous counts of the trie. */
 eh_status eh_count_selected(const eh_trie *trie, eh_sel_pattern pattern, uint32_t node, const eh_exec_opts *xopts,
                             void *stream, uint64_t *out_count);
+
+/* eh_trie_export_blocks -- host copy of the composite layout of a trie built
+ * with EH_BUILD_BLOCK_LAYOUT (EH_EINVAL otherwise).  *n_blocks and
+ * *n_bit_blocks are always written; each array is written when non-NULL:
+ *   off    n_vertices + 1 uint64: the directory of pruned set v (trie id) is
+ *          entries off[v] .. off[v+1]-1
+ *   dir    2 * n_blocks uint32, entry {block id (value / 256), info}: info bit 31
+ *          set = bitset block whose 8 words start at words[8 * (info & 0x7FFFFFFF)];
+ *          clear = uint block, the run of (info >> 23 & 255) + 1 values starting at
+ *          position info & 0x7FFFFF of the set's uint array (eh_trie_export)
+ *   words  8 * n_bit_blocks uint32, bit b of word i of a block = value 256 * id + 32 i + b */
+eh_status eh_trie_export_blocks(const eh_trie *trie, uint64_t *off, uint32_t *dir, uint32_t *words,
+                                uint64_t *n_blocks, uint64_t *n_bit_blocks);
 
 /* eh_count_batch -- n_queries independent queries in one persistent launch.
  * Each query's count goes to out_counts[i] and its status to out_status[i]

@@ -103,6 +103,9 @@ eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, 
         EH_TRY(st);
     } else if (pattern == EH_CLIQUE4) {
         EH_TRY(eh_launch_clique4(t, *plan, t->view(), xo, s, sc + SC_K4, sc + SC_CNT2, t->d_status, nullptr, 0));
+    } else if (pattern == EH_TRIANGLE && t->d_boff) {
+        // composite (block-level) layout
+        EH_TRY(eh_launch_tri_blocks(t, *plan, s, sc + SC_T, reinterpret_cast<unsigned int *>(sc + SC_CNT)));
     } else {
         int mode = pattern == EH_TRIANGLE ? M_COUNT : M_LOLLI;
         EH_TRY(eh_launch_triangle(t, *plan, t->view(), mode, xo, s, sc + SC_T, sc + SC_CNT, t->d_status, nullptr,

@@ -119,6 +119,11 @@ struct eh_trie {
     uint64_t n_words = 0;
     uint32_t *d_deg = nullptr;    // n, symmetric degree (new ids)
     uint64_t n_bitset = 0, n_nonempty = 0;
+    // composite (block-level) layout, EH_BUILD_BLOCK_LAYOUT only (blocks.cu)
+    uint64_t *d_boff = nullptr;   // n+1 directory offsets
+    uint2 *d_bdir = nullptr;      // {block id, info}
+    uint32_t *d_bwords = nullptr; // 8 words per bitset block
+    uint64_t n_blocks = 0, n_bit_blocks = 0;
     double density_skew = 0;
     uint64_t device_bytes = 0;
     std::vector<uint32_t> h_out_by_old;   // |N+(v)| by original id (host; serving footprints)
@@ -209,6 +214,11 @@ eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint3
 // (lo << nb | hi, original ids) and the degrees (order.cu)
 eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukeys, uint64_t m, uint32_t n, int nb,
                           const uint32_t *deg, uint32_t maxdeg, cudaStream_t s, uint32_t *new2old);
+// composite layout: build the directories of the pruned sets; the triangle
+// count over them (adds into d_acc; d_next = 2 zeroed counters) (blocks.cu)
+eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s);
+eh_status eh_launch_tri_blocks(eh_trie *t, const WorkPlan &plan, cudaStream_t s, unsigned long long *d_acc,
+                               unsigned int *d_next);
 // SK4 per-x sum over the selected vertex's neighbours (list.cu)
 eh_status eh_sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaStream_t s, uint64_t *total);
 eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,

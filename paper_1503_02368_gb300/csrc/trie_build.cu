@@ -184,6 +184,7 @@ void free_trie_arrays(eh_trie *t) {
     cudaFree(t->d_new2old); cudaFree(t->d_old2new); cudaFree(t->d_soff); cudaFree(t->d_snbr);
     cudaFree(t->d_desc); cudaFree(t->d_onbr); cudaFree(t->d_words); cudaFree(t->d_deg);
     cudaFree(t->d_scratch); cudaFree(t->d_status); cudaFree(t->d_arena);
+    cudaFree(t->d_boff); cudaFree(t->d_bdir); cudaFree(t->d_bwords);
     for (auto &kv : t->plans) { cudaFree(kv.second.d_heavy); cudaFree(kv.second.d_light); }
     t->plans.clear();
 }
@@ -353,7 +354,9 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_TRY(tmp.alloc(&woff, (uint64_t)n + 1));
     EH_TRY(tmp.alloc(&lo_word, (uint64_t)n + 1));
     EH_CUDA_TRY(cudaMemsetAsync(nwords, 0, ((uint64_t)n + 1) * 8, s));
-    if (n) k_layout<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, ooff, odeg, n, o.bitset_tau, o.min_bitset_len, nwords, lo_word);
+    // set-level bitsets, or none when the composite layout replaces them
+    const uint32_t set_tau = (o.flags & EH_BUILD_BLOCK_LAYOUT) ? 0u : o.bitset_tau;
+    if (n) k_layout<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, ooff, odeg, n, set_tau, o.min_bitset_len, nwords, lo_word);
     uint64_t tw = 0;
     EH_TRY(dev_exclusive_scan_u64(nwords, woff, (uint64_t)n + 1, s, &tw));
     t->n_words = tw;
@@ -400,6 +403,7 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
         if (hist[d] > best) { best = hist[d]; mode = d; }
     t->density_skew = var > 0 ? 3.0 * (mean - mode) / std::sqrt(var) : 0.0;
     t->device_bytes = bytes;
+    if (o.flags & EH_BUILD_BLOCK_LAYOUT) EH_TRY(eh_build_blocks(t, o.bitset_tau, s));
     return EH_OK;
 }
 

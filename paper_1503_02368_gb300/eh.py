@@ -16,6 +16,7 @@ PATTERNS = {"triangle": 0, "clique4": 1, "lollipop": 2, "lollipop_distinct": 3, 
 STATUS = {0: "EH_OK", 1: "EH_EINVAL", 2: "EH_ENOMEM", 3: "EH_ECUDA", 4: "EH_ETIMEOUT", 5: "EH_EOVERFLOW",
           6: "EH_EBUSY", 7: "EH_ECAPACITY"}
 EH_BUILD_DEVICE_INPUT = 1
+EH_BUILD_BLOCK_LAYOUT = 2
 
 
 class EHError(RuntimeError):
@@ -104,6 +105,8 @@ def lib():
     L.eh_count_status.argtypes = [vp, vp]
     L.eh_count_info_get.restype = st
     L.eh_count_info_get.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, ctypes.POINTER(CountInfo)]
+    L.eh_trie_export_blocks.restype = st
+    L.eh_trie_export_blocks.argtypes = [vp, u64p, u32p, u32p, u64p, u64p]
     L.eh_count_selected.restype = st
     L.eh_count_selected.argtypes = [vp, st, u32, ctypes.POINTER(ExecOpts), vp, u64p]
     L.eh_list.restype = st
@@ -201,7 +204,7 @@ class Trie:
     """Device-resident trie of a simple undirected graph (eh_build_trie)."""
 
     def __init__(self, src, dst, n_vertices, tau=32, min_bitset_len=0, stream=None, ordering="degree",
-                 order_seed=0):
+                 order_seed=0, block_layout=False):
         L = lib()
         self._h = ctypes.c_void_p(0)
         flags = 0
@@ -214,6 +217,8 @@ class Trie:
             dst = np.ascontiguousarray(dst, np.uint32)
             assert len(src) == len(dst)
             ps, pd, ne = src.ctypes.data, dst.ctypes.data, len(src)
+        if block_layout:
+            flags |= EH_BUILD_BLOCK_LAYOUT
         o = build_opts(tau, min_bitset_len, flags, ordering, order_seed)
         _check(L.eh_build_trie(ctypes.c_void_p(ps), ctypes.c_void_p(pd), ne, n_vertices, ctypes.byref(o),
                                _stream(stream), ctypes.byref(self._h)))
@@ -314,6 +319,17 @@ class Trie:
                                 _u32p(bnw), _u64p(boff), _u32p(words)))
         return {"new_to_old": new2old, "off": off, "len": ln, "nbr": nbr, "bits_lo": blo, "bits_nwords": bnw,
                 "bits_off": boff, "words": words}
+
+    def export_blocks(self):
+        """Host copy of the composite layout: (off[n+1], dir[n_blocks, 2], words[n_bit_blocks, 8])."""
+        nb, nbit = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        L = lib()
+        _check(L.eh_trie_export_blocks(self._h, None, None, None, ctypes.byref(nb), ctypes.byref(nbit)))
+        off = np.zeros(self.n + 1, np.uint64)
+        d = np.zeros((max(nb.value, 1), 2), np.uint32)
+        w = np.zeros((max(nbit.value, 1), 8), np.uint32)
+        _check(L.eh_trie_export_blocks(self._h, _u64p(off), _u32p(d), _u32p(w), ctypes.byref(nb), ctypes.byref(nbit)))
+        return off, d[:nb.value], w[:nbit.value]
 
     def count_batch(self, patterns, offsets, pool, mode=0, xopts=None, stream=None):
         """Queries i = (patterns[i], pool[offsets[i]:offsets[i+1]]); returns (counts, statuses)."""

@@ -181,21 +181,30 @@ eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s) {
     EH_TRY(dev_alloc(&nblk, (uint64_t)n + 1, s));
     eh_status st = dev_alloc(&nbit, (uint64_t)n + 1, s);
     uint64_t total = 0, total_bit = 0;
-    if (st == EH_OK && cudaMemsetAsync(nblk, 0, ((uint64_t)n + 1) * 8, s) != cudaSuccess) st = EH_ECUDA;
-    if (st == EH_OK && cudaMemsetAsync(nbit, 0, ((uint64_t)n + 1) * 8, s) != cudaSuccess) st = EH_ECUDA;
-    if (st == EH_OK && n) k_blk_count<<<blocks(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, nblk, nbit);
+    auto cuda_ok = [&](cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return true;
+        eh_set_error("block layout: %s: %s", what, cudaGetErrorString(e));
+        st = EH_ECUDA;
+        return false;
+    };
+    if (st == EH_OK) cuda_ok(cudaMemsetAsync(nblk, 0, ((uint64_t)n + 1) * 8, s), "memset");
+    if (st == EH_OK) cuda_ok(cudaMemsetAsync(nbit, 0, ((uint64_t)n + 1) * 8, s), "memset");
+    if (st == EH_OK && n) {
+        k_blk_count<<<blocks(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, nblk, nbit);
+        cuda_ok(cudaGetLastError(), "count launch");
+    }
     if (st == EH_OK) st = trie_alloc(&t->d_boff, (uint64_t)n + 1);
     if (st == EH_OK) st = dev_exclusive_scan_u64(nblk, t->d_boff, (uint64_t)n + 1, s, &total);
     if (st == EH_OK) st = dev_exclusive_scan_u64(nbit, nbit, (uint64_t)n + 1, s, &total_bit);
     if (st == EH_OK && total_bit >= BLK_BIT) { eh_set_error("block layout: too many bitset blocks"); st = EH_EINVAL; }
     if (st == EH_OK) st = trie_alloc(&t->d_bdir, total);
     if (st == EH_OK) st = trie_alloc(&t->d_bwords, total_bit * 8);
-    if (st == EH_OK && cudaMemsetAsync(t->d_bwords, 0, (total_bit ? total_bit : 1) * 32, s) != cudaSuccess)
-        st = EH_ECUDA;
-    if (st == EH_OK && n)
+    if (st == EH_OK && total_bit) cuda_ok(cudaMemsetAsync(t->d_bwords, 0, total_bit * 32, s), "memset");
+    if (st == EH_OK && n) {
         k_blk_fill<<<blocks(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, t->d_boff, nbit, t->d_bdir, t->d_bwords);
-    if (st == EH_OK && cudaGetLastError() != cudaSuccess) st = EH_ECUDA;
-    if (st == EH_OK && cudaStreamSynchronize(s) != cudaSuccess) st = EH_ECUDA;
+        cuda_ok(cudaGetLastError(), "fill launch");
+    }
+    if (st == EH_OK) cuda_ok(cudaStreamSynchronize(s), "synchronize");
     dev_free(nblk, s);
     dev_free(nbit, s);
     if (st != EH_OK) return st;

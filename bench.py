@@ -243,12 +243,27 @@ def bench_clique4(eh, reps=5):
     trie.status()
     ms_b = s0.elapsed_time(s1) / reps
     cb = int(out.item())
+    # selection queries (Sec. 5.3) with the selected vertex = the 1000th-highest degree
+    import numpy as np
+    deg = np.zeros(g["n"], np.int64)
+    np.add.at(deg, g["src"], 1)
+    np.add.at(deg, g["dst"], 1)
+    node = int(np.argsort(-deg, kind="stable")[1000])
+    sel = {"node": node}
+    for p in ("clique4", "barbell"):
+        trie.count_selected(p, node)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c_sel = trie.count_selected(p, node)
+        sel[p] = {"count": c_sel, "ms": (time.perf_counter() - t0) * 1e3}
+    sel["timing"] = "host clock around one synchronous eh_count_selected"
     trie.close()
     return {"workload": "chunglu_n1000000_g2.1 (w_max 5e4, mean degree 40) 4-clique", "m_unique_edges": m,
             "count": c, "exact_vs_oracle": c == gold["clique4"], "ms": ms, "edges_per_s": m / (ms / 1e3),
             "cliques_per_s": c / (ms / 1e3), "tau": 32, "cta_warps": 16,
             "barbell": {"count": cb, "exact_vs_oracle": cb == gold.get("barbell"), "ms": ms_b,
-                        "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"}}
+                        "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"},
+            "selection": sel}
 
 
 def bench_list(eh, trie, xo, alg_bytes, gold, reps=3):

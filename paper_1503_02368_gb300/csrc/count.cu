@@ -28,7 +28,7 @@ using namespace ehd;
 
 constexpr uint32_t BM_CAP_WORDS = 8192;        // 32 KB on-chip bitmap: value ranges up to 262,144
 
-enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2 };
+enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2, M_APEX = TRI_MODE_APEX };
 
 struct Acc {
     unsigned long long t;   // triangles
@@ -49,7 +49,7 @@ __device__ __forceinline__ void on_match(Acc &acc, uint32_t w, uint32_t duv, con
 template <int MODE>
 __device__ __forceinline__ void on_word(Acc &acc, uint32_t x, uint32_t base, uint32_t duv, const TrieView &tv,
                                         unsigned long long *vt) {
-    if (MODE == M_COUNT) {
+    if (MODE == M_COUNT || MODE == M_APEX) {
         acc.t += __popc(x);
     } else {
         while (x) {
@@ -440,6 +440,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
     extern __shared__ __align__(16) uint32_t sA[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_item, s_next;
+    __shared__ unsigned long long s_red[MODE == M_APEX ? WARPS : 1];
     const int tid = threadIdx.x, lane = tid & 31;
     Acc acc{0, 0};
     uint32_t phase = 0;
@@ -452,7 +453,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
+        const unsigned long long t0 = acc.t;
         if (!tri_heavy<MODE, WARPS>(tv, heavy[item], ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
+        if (MODE == M_APEX) {   // this vertex's triangles (as the largest id) to vt[item]
+            unsigned long long d = acc.t - t0;
+            for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
+            if (lane == 0) s_red[tid >> 5] = d;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long c = 0;
+                for (int w = 0; w < WARPS; ++w) c += s_red[w];
+                vt[item] = c;
+            }
+        }
     }
 
     // light vertices: one warp each, taken 32 at a time
@@ -462,7 +475,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         base = __shfl_sync(FULL, base, 0);
         if (base >= n_light) break;
         uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
-        for (uint32_t i = (uint32_t)base; i < end; ++i) light_vertex<MODE>(tv, __ldg(&light[i]), ratio, acc, vt);
+        for (uint32_t i = (uint32_t)base; i < end; ++i) {
+            const unsigned long long t0 = acc.t;
+            light_vertex<MODE>(tv, __ldg(&light[i]), ratio, acc, vt);
+            if (MODE == M_APEX) {   // vt[n_heavy + i]
+                unsigned long long d = acc.t - t0;
+                for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
+                if (lane == 0) vt[n_heavy + i] = d;
+            }
+        }
     }
 
     // reduce: warp, then one atomic per warp
@@ -1038,6 +1059,7 @@ eh_status eh_launch_triangle(const eh_trie *t, const WorkPlan &plan, TrieView tv
         case M_COUNT: return launch_tri_w<M_COUNT>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
         case M_LOLLI: return launch_tri_w<M_LOLLI>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
         case M_VERTEX: return launch_tri_w<M_VERTEX>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        case M_APEX: return launch_tri_w<M_APEX>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
     }
     eh_set_error("unknown triangle mode %d", mode);
     return EH_EINVAL;

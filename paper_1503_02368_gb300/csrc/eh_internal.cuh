@@ -193,6 +193,10 @@ int eh_num_sms();
 
 // Count entry points shared between files.
 eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan **out);
+// eh_launch_triangle modes: 0 count, 1 lollipop, 2 per-vertex t (d_vt[n]),
+// TRI_MODE_APEX: each work item's triangles in which it is the largest id, to
+// d_vt[item] for heavy items and d_vt[n_heavy + i] for light item i
+constexpr int TRI_MODE_APEX = 3;
 eh_status eh_launch_triangle(const eh_trie *t, const WorkPlan &plan, TrieView tv, int mode,
                              const eh_exec_opts &xo, cudaStream_t s, unsigned long long *d_acc,
                              unsigned long long *d_counters, uint32_t *d_status, unsigned long long *d_vt,

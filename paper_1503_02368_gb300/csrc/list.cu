@@ -70,7 +70,10 @@ struct Sink {
     unsigned long long *s_cur;   // write pass, heavy item: the CTA's cursor (device memory); null if light
     unsigned long long end;      // write pass: end of the item's range
     uint32_t key[3];             // caller ids of the bound prefix: u, v (and z)
+    uint32_t *stage;             // write pass: this warp's rows of the current round (shared memory)
 };
+
+constexpr uint32_t STAGE_ROWS = 128;   // rows one round can produce (four candidates per lane)
 
 __device__ __forceinline__ void sort2(uint32_t &a, uint32_t &b) {
     const uint32_t lo = min(a, b), hi = max(a, b);
@@ -78,22 +81,38 @@ __device__ __forceinline__ void sort2(uint32_t &a, uint32_t &b) {
     b = hi;
 }
 
+// row r of the round in the warp's staging buffer: the clique's caller ids, ascending
 template <int W>
-__device__ __forceinline__ void put_row(const ListArgs &a, const Sink &sk, unsigned long long pos, uint32_t w_new) {
-    if (pos >= sk.end || pos >= a.cap) {   // the two passes disagree: never write outside the item's range
-        atomicOr(a.status, DEV_ST_RANGE);
-        return;
-    }
+__device__ __forceinline__ void stage_row(const ListArgs &a, const Sink &sk, uint32_t r, uint32_t w_new) {
     uint32_t x0 = sk.key[0], x1 = sk.key[1], x2 = __ldg(&a.new2old[w_new]);
+    uint32_t *o = sk.stage + r * W;
     if (W == P_TRI) {
         sort2(x0, x1); sort2(x1, x2); sort2(x0, x1);
-        uint32_t *o = a.out + 3 * pos;
         o[0] = x0; o[1] = x1; o[2] = x2;
     } else {
         uint32_t x3 = sk.key[2];
         sort2(x0, x1); sort2(x2, x3); sort2(x0, x2); sort2(x1, x3); sort2(x1, x2);
-        *reinterpret_cast<uint4 *>(a.out + 4 * pos) = make_uint4(x0, x1, x2, x3);
+        *reinterpret_cast<uint4 *>(o) = make_uint4(x0, x1, x2, x3);
     }
+}
+
+// the round's `total` staged rows to rows base .. base+total-1 of the output,
+// consecutive lanes on consecutive words (never outside the item's range)
+template <int W>
+__device__ __forceinline__ void flush(const ListArgs &a, const Sink &sk, unsigned long long base, uint32_t total) {
+    const uint32_t lane = threadIdx.x & 31;
+    __syncwarp();
+    if (base + total > sk.end || base + total > a.cap) {   // the two passes disagree
+        if (lane == 0) atomicOr(a.status, DEV_ST_RANGE);
+    } else if (W == P_K4) {
+        uint4 *o = reinterpret_cast<uint4 *>(a.out + base * 4);
+        const uint4 *st = reinterpret_cast<const uint4 *>(sk.stage);
+        for (uint32_t i = lane; i < total; i += 32) o[i] = st[i];
+    } else {
+        uint32_t *o = a.out + base * 3;
+        for (uint32_t i = lane; i < total * 3; i += 32) o[i] = sk.stage[i];
+    }
+    __syncwarp();
 }
 
 // first output row of a round whose matches total `total` (warp-uniform);
@@ -121,11 +140,15 @@ __device__ __forceinline__ unsigned long long reserve(Sink &sk, uint32_t total) 
 template <int W, bool EMIT>
 __device__ __forceinline__ void emit_one(const ListArgs &a, Sink &sk, bool hit, uint32_t w) {
     const uint32_t b = __ballot_sync(FULL, hit);
-    const unsigned long long base = reserve<EMIT>(sk, __popc(b));
-    if (EMIT && hit) {
-        const uint32_t lane = threadIdx.x & 31;
-        put_row<W>(a, sk, base + __popc(b & ((1u << lane) - 1u)), w);
+    const uint32_t total = __popc(b);
+    if (!EMIT) {
+        sk.n += total;
+        return;
     }
+    if (!total) return;
+    const unsigned long long base = reserve<EMIT>(sk, total);
+    if (hit) stage_row<W>(a, sk, __popc(b & ((1u << (threadIdx.x & 31)) - 1u)), w);
+    flush<W>(a, sk, base, total);
 }
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
@@ -157,12 +180,14 @@ __device__ __forceinline__ void emit_four(const ListArgs &a, Sink &sk, uint32_t 
     }
     uint32_t total;
     const uint32_t r = warp_excl(k, total);
+    if (!total) return;
     const unsigned long long base = reserve<EMIT>(sk, total);
     const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
     uint32_t i = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-        if ((m >> c) & 1u) put_row<W>(a, sk, base + r + i++, vv[c]);
+        if ((m >> c) & 1u) stage_row<W>(a, sk, r + i++, vv[c]);
+    flush<W>(a, sk, base, total);
 }
 
 // x in the set with descriptor d (bit probe of its bitset, else binary search of its uint array)
@@ -353,6 +378,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
     uint32_t *S = nullptr;
     if (W == P_K4) S = smem + LA_CAP_WORDS + warp * S_CAP;
     uint32_t *S_big = a.arena ? a.arena + (uint64_t)(blockIdx.x * LIST_WARPS + warp) * a.arena_stride : nullptr;
+    uint32_t *stage = EMIT ? smem + LA_CAP_WORDS + (W == P_K4 ? LIST_WARPS * S_CAP : 0) + warp * STAGE_ROWS * W
+                           : nullptr;
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(a.next_item, 1u);
@@ -373,6 +400,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
         sk.n = 0;
         sk.cur = 0;
         sk.s_cur = EMIT ? a.cursor + blockIdx.x : nullptr;
+        sk.stage = stage;
         sk.end = EMIT ? a.offs[item + 1] : 0;
         sk.key[0] = __ldg(&a.new2old[u]);
         for (;;) {
@@ -418,6 +446,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
 // Light items: one warp each, A = N+(u) one element per lane (|A| <= 32).
 template <int W, bool EMIT>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
+    __shared__ __align__(16) uint32_t s_stage[EMIT ? LIST_WARPS * 32 * W : 4];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t item = blockIdx.x * LIST_WARPS + (threadIdx.x >> 5);
     if (item >= a.n_light) return;
@@ -431,6 +460,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
     Sink sk;
     sk.n = 0;
     sk.s_cur = nullptr;
+    sk.stage = s_stage + (threadIdx.x >> 5) * 32 * W;
     sk.cur = EMIT ? a.offs[a.n_heavy + item] : 0;
     sk.end = EMIT ? a.offs[a.n_heavy + item + 1] : 0;
     sk.key[0] = __ldg(&a.new2old[u]);
@@ -461,7 +491,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
 
 template <int W, bool EMIT>
 eh_status launch_pass(const ListArgs &a, uint32_t heavy_grid, cudaStream_t s) {
-    const uint32_t smem = LA_CAP_WORDS * 4 + (W == P_K4 ? LIST_WARPS * S_CAP * 4 : 0);
+    const uint32_t smem = LA_CAP_WORDS * 4 + (W == P_K4 ? LIST_WARPS * S_CAP * 4 : 0) +
+                          (EMIT ? LIST_WARPS * STAGE_ROWS * W * 4 : 0);
     EH_CUDA_TRY(cudaFuncSetAttribute(k_list_heavy<W, EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     if (a.n_heavy) k_list_heavy<W, EMIT><<<heavy_grid, LIST_WARPS * 32, smem, s>>>(a);
     EH_CUDA_TRY(cudaGetLastError());
@@ -484,7 +515,7 @@ eh_status heavy_grid_size(uint32_t n_heavy, uint32_t *grid) {
 struct ListBuffers {
     unsigned long long *cnt = nullptr, *offs = nullptr;
     unsigned int *next = nullptr;
-    unsigned long long *cursor = nullptr;
+    unsigned long long *cursor = nullptr, *scr = nullptr;
     uint32_t *arena = nullptr;
     cudaStream_t s = nullptr;
     ~ListBuffers() {
@@ -492,6 +523,7 @@ struct ListBuffers {
         dev_free(offs, s);
         dev_free(next, s);
         dev_free(cursor, s);
+        dev_free(scr, s);
         dev_free(arena, s);
         cudaStreamSynchronize(s);
     }
@@ -512,9 +544,12 @@ __global__ void k_gather_u32(const uint32_t *__restrict__ idx, uint32_t n, const
 }
 
 // Count pass (and, when d_out is set, the write pass) over the items.
+// plan: the whole-graph work plan the items come from, or null.  With a plan,
+// the triangle rows per item come from the count kernel's per-item mode (the
+// same items, the same numbers: the triangles whose largest id is the item).
 template <int W>
-eh_status run_items(eh_trie *t, const Items &it, const eh_exec_opts &xo, cudaStream_t s, uint32_t *d_out,
-                    uint64_t capacity, uint64_t *out_n) {
+eh_status run_items(eh_trie *t, const Items &it, const WorkPlan *plan, const eh_exec_opts &xo, cudaStream_t s,
+                    uint32_t *d_out, uint64_t capacity, uint64_t *out_n) {
     const uint64_t n_items = (uint64_t)it.n_heavy + it.n_light;
     ListBuffers b;
     b.s = s;
@@ -554,7 +589,14 @@ eh_status run_items(eh_trie *t, const Items &it, const eh_exec_opts &xo, cudaStr
     a.next_item = b.next;
     a.cnt = b.cnt;
     a.offs = nullptr;
-    EH_TRY((launch_pass<W, false>(a, grid, s)));
+    if (W == P_TRI && plan && !it.a_off) {
+        EH_TRY(dev_alloc(&b.scr, 4, s));
+        EH_CUDA_TRY(cudaMemsetAsync(b.scr, 0, 32, s));
+        EH_TRY(eh_launch_triangle(t, *plan, t->view(), TRI_MODE_APEX, xo, s, b.scr, b.scr + 1, t->d_status, b.cnt,
+                                  nullptr));
+    } else {
+        EH_TRY((launch_pass<W, false>(a, grid, s)));
+    }
     uint64_t total = 0;
     EH_TRY(dev_exclusive_scan_u64(reinterpret_cast<const uint64_t *>(b.cnt), reinterpret_cast<uint64_t *>(b.offs),
                                   n_items + 1, s, &total));
@@ -584,7 +626,7 @@ eh_status run_list(eh_trie *t, const eh_exec_opts &xo, cudaStream_t s, uint32_t 
     it.n_heavy = plan->n_heavy;
     it.light = plan->d_light;
     it.n_light = plan->n_light;
-    return run_items<W>(t, it, xo, s, d_out, capacity, out_n);
+    return run_items<W>(t, it, plan, xo, s, d_out, capacity, out_n);
 }
 
 // 4-cliques through each x in N(node): the triangles of G[N(x)], counted by
@@ -635,7 +677,7 @@ eh_status sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaS
         it.a_off = t->d_soff;
         it.a_nbr = t->d_snbr;
         it.a_len = t->d_deg;
-        st = run_items<P_K4>(t, it, xo, s, nullptr, 0, total);
+        st = run_items<P_K4>(t, it, nullptr, xo, s, nullptr, 0, total);
     } else {
         eh_set_error("sk4: copying the selected items failed");
     }

@@ -55,6 +55,7 @@ struct ListArgs {
     const uint32_t *a_len;
     unsigned int *next_item;               // heavy items taken so far
     unsigned long long *cursor;            // write pass: next row of each heavy CTA's current item
+    uint32_t rel32;                        // 1: an item's rows fit 32 bits (shared-memory cursor instead)
     unsigned long long *cnt;               // count pass: rows per item (heavy items, then light)
     const unsigned long long *offs;        // write pass: first row of each item (n_items + 1 entries)
     uint32_t *out;                         // rows of width 3 or 4
@@ -68,6 +69,8 @@ struct Sink {
     unsigned long long n;        // count pass: rows found by this warp
     unsigned long long cur;      // write pass, light item: next row of the warp
     unsigned long long *s_cur;   // write pass, heavy item: the CTA's cursor (device memory); null if light
+    uint32_t *s_rel;             // write pass, heavy item: rows taken so far (shared memory), when 32 bits suffice
+    unsigned long long rel_base; //   ... counted from this first row of the item
     unsigned long long end;      // write pass: end of the item's range
     uint32_t key[3];             // caller ids of the bound prefix: u, v (and z)
     uint32_t *stage;             // write pass: this warp's rows of the current round (shared memory)
@@ -125,7 +128,11 @@ __device__ __forceinline__ unsigned long long reserve(Sink &sk, uint32_t total) 
     }
     unsigned long long base = 0;
     if (total) {
-        if (sk.s_cur) {
+        if (sk.s_rel) {
+            uint32_t r = 0;
+            if ((threadIdx.x & 31) == 0) r = atomicAdd(sk.s_rel, total);
+            base = sk.rel_base + __shfl_sync(FULL, r, 0);
+        } else if (sk.s_cur) {
             if ((threadIdx.x & 31) == 0) base = atomicAdd(sk.s_cur, (unsigned long long)total);
             base = __shfl_sync(FULL, base, 0);
         } else {
@@ -372,7 +379,7 @@ template <int W, bool EMIT>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sA = smem;
-    __shared__ uint32_t s_item, s_next;
+    __shared__ uint32_t s_item, s_next, s_rel;
     __shared__ unsigned long long s_wcnt[LIST_WARPS];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *S = nullptr;
@@ -384,7 +391,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(a.next_item, 1u);
             s_next = 1;
-            if (EMIT && s_item < a.n_heavy) atomicExch(a.cursor + blockIdx.x, a.offs[s_item]);
+            s_rel = 0;
+            if (EMIT && !a.rel32 && s_item < a.n_heavy) atomicExch(a.cursor + blockIdx.x, a.offs[s_item]);
         }
         __syncthreads();
         const uint32_t item = s_item;
@@ -399,7 +407,9 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
         Sink sk;
         sk.n = 0;
         sk.cur = 0;
-        sk.s_cur = EMIT ? a.cursor + blockIdx.x : nullptr;
+        sk.s_cur = EMIT && !a.rel32 ? a.cursor + blockIdx.x : nullptr;
+        sk.s_rel = EMIT && a.rel32 ? &s_rel : nullptr;
+        sk.rel_base = EMIT ? a.offs[item] : 0;
         sk.stage = stage;
         sk.end = EMIT ? a.offs[item + 1] : 0;
         sk.key[0] = __ldg(&a.new2old[u]);
@@ -460,6 +470,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
     Sink sk;
     sk.n = 0;
     sk.s_cur = nullptr;
+    sk.s_rel = nullptr;
+    sk.rel_base = 0;
     sk.stage = s_stage + (threadIdx.x >> 5) * 32 * W;
     sk.cur = EMIT ? a.offs[a.n_heavy + item] : 0;
     sk.end = EMIT ? a.offs[a.n_heavy + item + 1] : 0;
@@ -583,6 +595,11 @@ eh_status run_items(eh_trie *t, const Items &it, const WorkPlan *plan, const eh_
     }
     a.status = t->d_status;
     a.cursor = b.cursor;
+    {   // rows of one item: at most C(|A|, 2) triangles or C(|A|, 3) 4-cliques
+        const double L = it.a_off ? (double)t->max_deg : (double)t->max_out;
+        const double bound = W == P_TRI ? L * (L - 1) / 2 : L * (L - 1) * (L - 2) / 6;
+        a.rel32 = bound < 4294967295.0 ? 1u : 0u;
+    }
     a.out = d_out;
     a.cap = capacity;
     // pass 1: rows per item

@@ -9,12 +9,17 @@
 // light bound is taken by a CTA, which stages A = N+(u) in shared memory (a
 // bitmap when its value range fits, else the sorted array) and whose warps take the
 // v in A dynamically; a lighter u is taken by one warp holding A one element
-// per lane.  Two passes run the same traversal.  The first stores each item's
-// number of rows, an exclusive scan turns those into output ranges, and the
-// second writes the rows.  Inside an item the lanes of a warp take positions
-// from ballot / prefix-sum ranks and the warps of a CTA reserve runs from a
-// shared-memory cursor: the output is dense, needs no global atomics, and the
-// rows of an item fill exactly the range the first pass gave it.
+// per lane.  Two passes.  The first stores each item's number of rows (for
+// triangles, the count kernel's per-item mode gives them; for 4-cliques, this
+// file's traversal in counting mode), an exclusive scan turns those into
+// output ranges, and the second pass runs the traversal again and writes the
+// rows.  Inside an item the lanes of a warp take positions from ballot /
+// prefix-sum ranks, stage the round's rows in shared memory and store them
+// as one contiguous run; the warps of a CTA reserve runs from a shared-memory
+// cursor (a device-memory one when an item's rows could pass 2^32).  The
+// output is dense and the rows of an item fill exactly the range the first
+// pass gave it.  The same 4-clique passes, fed with A = N(x) for the
+// neighbours x of a selected vertex, count the selection query SK4.
 //
 // Per pair the intersection works on what the lanes can enumerate (Sec. 4.2's
 // operations): with A as an on-chip bitmap every element of N+(v) probes one

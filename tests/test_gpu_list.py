@@ -240,3 +240,25 @@ def test_rmat22_triangles_full_size(eh):
         got = lexsorted(rows[mask].cpu().numpy().view(np.uint32))
         assert np.array_equal(got, lexsorted(o.list_triangles_at(v))), v
     assert_unique_triangles(rows, 22)
+
+
+def test_chunglu_triangles_full_size(eh):
+    # 332 M rows (4 GB): the oracle's count, every row a triangle of the input, no repeats
+    # (ids < 2^20: a row packs into one 64-bit key), rows at sampled vertices as the oracle's
+    import torch
+    g = W.chunglu_1m()
+    gold = GOLD["chunglu_n1000000_g2.1"]
+    t = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    rows = t.list("triangle")
+    assert rows.shape[0] == gold["triangle"]
+    assert_rows_are_cliques(rows, edge_keys(g))
+    r = rows.to(torch.int64)
+    key = torch.sort((r[:, 0] << 40) | (r[:, 1] << 20) | r[:, 2]).values
+    del r
+    assert not bool((key[1:] == key[:-1]).any())
+    del key
+    o = oracle.Graph(g["n"], g["src"], g["dst"])
+    deg = o.degrees()
+    for v in [int(x) for x in np.nonzero((deg >= 40) & (deg <= 200))[0][::50000][:8]]:
+        got = lexsorted(rows[(rows == v).any(dim=1)].cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, lexsorted(o.list_triangles_at(v))), v

@@ -326,7 +326,9 @@ struct Level1 {
     __device__ __forceinline__ void sorted(const uint32_t *A, uint32_t j, const SetDesc &dv) {
         const TrieView &tv = a.tv;
         const uint32_t lane = threadIdx.x & 31;
-        if (dv.nwords || (uint64_t)dv.len > (uint64_t)a.ratio * j) {
+        // the smaller side enumerates (the min property of Sec. 4.2): A's prefix probes
+        // N+(v) when it is no longer than N+(v) (bit probes) or far shorter (binary search)
+        if ((uint64_t)dv.len > (uint64_t)a.ratio * j || (dv.nwords && j <= dv.len)) {
             // A's elements probe N+(v): its bitset, or a binary search of its uint array
             for (uint32_t i0 = 0; i0 < j; i0 += 32) {
                 const uint32_t i = i0 + lane;
@@ -356,7 +358,7 @@ __device__ __forceinline__ void k4_level2(const ListArgs &a, Sink &sk, const uin
                                           const SetDesc &dz) {
     const uint32_t lane = threadIdx.x & 31;
     if (dz.len == 0 || r == 0) return;
-    if (dz.nwords || (uint64_t)dz.len > (uint64_t)a.ratio * r) {
+    if ((uint64_t)dz.len > (uint64_t)a.ratio * r || (dz.nwords && r <= dz.len)) {   // the smaller side enumerates
         for (uint32_t i0 = 0; i0 < r; i0 += 32) {
             const uint32_t i = i0 + lane;
             const uint32_t x = i < r ? S[i] : EH_PAD;

@@ -24,8 +24,6 @@ namespace {
 
 constexpr uint32_t BLK_BIT = 0x80000000u;
 
-inline unsigned blocks(uint64_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
-
 // persistent trie memory (released with the trie by cudaFree)
 template <typename T>
 eh_status trie_alloc(T **p, uint64_t count) {
@@ -190,7 +188,7 @@ eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s) {
     if (st == EH_OK) cuda_ok(cudaMemsetAsync(nblk, 0, ((uint64_t)n + 1) * 8, s), "memset");
     if (st == EH_OK) cuda_ok(cudaMemsetAsync(nbit, 0, ((uint64_t)n + 1) * 8, s), "memset");
     if (st == EH_OK && n) {
-        k_blk_count<<<blocks(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, nblk, nbit);
+        k_blk_count<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, nblk, nbit);
         cuda_ok(cudaGetLastError(), "count launch");
     }
     if (st == EH_OK) st = trie_alloc(&t->d_boff, (uint64_t)n + 1);
@@ -201,7 +199,7 @@ eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s) {
     if (st == EH_OK) st = trie_alloc(&t->d_bwords, total_bit * 8);
     if (st == EH_OK && total_bit) cuda_ok(cudaMemsetAsync(t->d_bwords, 0, total_bit * 32, s), "memset");
     if (st == EH_OK && n) {
-        k_blk_fill<<<blocks(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, t->d_boff, nbit, t->d_bdir, t->d_bwords);
+        k_blk_fill<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, t->d_boff, nbit, t->d_bdir, t->d_bwords);
         cuda_ok(cudaGetLastError(), "fill launch");
     }
     if (st == EH_OK) cuda_ok(cudaStreamSynchronize(s), "synchronize");

@@ -99,25 +99,6 @@ __device__ __forceinline__ void pair_bitmap(const TrieView &tv, const uint32_t *
     }
 }
 
-// Descriptor of lane `src` broadcast to the warp (descriptors of upcoming
-// pairs are loaded one per lane, in parallel, then handed out pair by pair).
-__device__ __forceinline__ SetDesc bcast_desc(const SetDesc &d, int src) {
-    SetDesc r;
-    r.off = __shfl_sync(FULL, d.off, src);
-    r.len = __shfl_sync(FULL, d.len, src);
-    r.deg = __shfl_sync(FULL, d.deg, src);
-    r.woff = __shfl_sync(FULL, d.woff, src);
-    r.lo_word = __shfl_sync(FULL, d.lo_word, src);
-    r.nwords = __shfl_sync(FULL, d.nwords, src);
-    return r;
-}
-
-__device__ __forceinline__ SetDesc empty_desc() {
-    SetDesc d;
-    d.off = 0; d.len = 0; d.deg = 0; d.woff = 0; d.lo_word = 0; d.nwords = 0;
-    return d;
-}
-
 // A sorted array (shared or global), effective prefix A[0..j) ∩ B
 template <int MODE>
 __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *A, uint32_t j, const SetDesc &dv,

@@ -1,10 +1,13 @@
 // dev_util.cuh -- device helpers shared by the intersection kernels: 128-bit
 // read-only loads, the bulk global->shared copy with its mbarrier, the bounded
-// wait on that barrier, and a lower-bound search.
+// wait on that barrier, a lower-bound search, and the warp broadcast of a set
+// descriptor.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "eh_internal.cuh"
 
 namespace ehd {
 
@@ -68,6 +71,25 @@ __device__ __forceinline__ uint32_t lower_bound(const uint32_t *A, uint32_t lo, 
         if (A[mid] < key) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// descriptor held by lane `src`, broadcast to the warp (descriptors of upcoming
+// pairs are loaded one per lane, in parallel, then handed out pair by pair)
+__device__ __forceinline__ SetDesc bcast_desc(const SetDesc &d, int src) {
+    SetDesc r;
+    r.off = __shfl_sync(FULL, d.off, src);
+    r.len = __shfl_sync(FULL, d.len, src);
+    r.deg = __shfl_sync(FULL, d.deg, src);
+    r.woff = __shfl_sync(FULL, d.woff, src);
+    r.lo_word = __shfl_sync(FULL, d.lo_word, src);
+    r.nwords = __shfl_sync(FULL, d.nwords, src);
+    return r;
+}
+
+__device__ __forceinline__ SetDesc empty_desc() {
+    SetDesc d;
+    d.off = 0; d.len = 0; d.deg = 0; d.woff = 0; d.lo_word = 0; d.nwords = 0;
+    return d;
 }
 
 }  // namespace ehd

@@ -189,6 +189,16 @@ void dev_free(T *&p, cudaStream_t s) {
 
 static inline uint32_t ceil_div_u32(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
+// blocks of t threads covering n items
+static inline unsigned blocks_for(uint64_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// bits to represent values in [0, n)
+static inline int bits_for(uint64_t n) {
+    int b = 1;
+    while (b < 63 && (1ull << b) < n) ++b;
+    return b;
+}
+
 int eh_num_sms();
 
 // Count entry points shared between files.

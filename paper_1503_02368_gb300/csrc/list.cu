@@ -213,17 +213,6 @@ __device__ __forceinline__ bool in_set(const TrieView &tv, const SetDesc &d, uin
     return p < d.len && __ldg(&B[p]) == x;
 }
 
-__device__ __forceinline__ SetDesc bcast_desc(const SetDesc &d, int src) {
-    SetDesc r;
-    r.off = __shfl_sync(FULL, d.off, src);
-    r.len = __shfl_sync(FULL, d.len, src);
-    r.deg = __shfl_sync(FULL, d.deg, src);
-    r.woff = __shfl_sync(FULL, d.woff, src);
-    r.lo_word = __shfl_sync(FULL, d.lo_word, src);
-    r.nwords = __shfl_sync(FULL, d.nwords, src);
-    return r;
-}
-
 // ------------------------------------------------------------ staged A
 
 struct StagedA {
@@ -471,8 +460,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
     const uint32_t *Ag = a.a_off ? a.a_nbr + a.a_off[u] : a.tv.nbr + a.tv.desc[u].off;
     const uint32_t L = min(a.a_off ? a.a_len[u] : a.tv.desc[u].len, 32u);
     const uint32_t x = lane < L ? __ldg(&Ag[lane]) : EH_PAD;
-    SetDesc mine;
-    mine.off = 0; mine.len = 0; mine.deg = 0; mine.woff = 0; mine.lo_word = 0; mine.nwords = 0;
+    SetDesc mine = empty_desc();
     if (lane < L) mine = a.tv.desc[x];
     Sink sk;
     sk.n = 0;

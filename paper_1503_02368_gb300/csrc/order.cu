@@ -33,14 +33,6 @@ namespace {
 
 constexpr uint32_t UNSEEN = 0xFFFFFFFFu;
 
-inline unsigned blocks(uint64_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
-
-int bits_of(uint64_t n) {   // bits to represent values in [0, n)
-    int b = 1;
-    while (b < 63 && (1ull << b) < n) ++b;
-    return b;
-}
-
 // SplitMix64 (Steele, Lea, Flood 2014), one output for a counter value
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -201,7 +193,7 @@ eh_status sort_to_order(uint64_t **keys, uint64_t **tmp, uint32_t n, int key_bit
                         uint32_t *order) {
     if (!n) return EH_OK;
     EH_TRY(dev_radix_sort_u64(keys, tmp, n, std::min(64, key_bits), s));
-    k_low_bits<<<blocks(n), 256, 0, s>>>(*keys, n, nb, order);
+    k_low_bits<<<blocks_for(n), 256, 0, s>>>(*keys, n, nb, order);
     EH_CUDA_TRY(cudaGetLastError());
     return EH_OK;
 }
@@ -214,10 +206,10 @@ eh_status old_csr(const uint64_t *ukeys, uint64_t m, uint32_t n, int nb, const u
     EH_TRY(sc.alloc(&dk2, 2 * m));
     EH_TRY(sc.alloc(&wide, (uint64_t)n + 1));
     EH_TRY(sc.alloc(off, (uint64_t)n + 1));
-    if (m) k_sym_keys<<<blocks(m), 256, 0, s>>>(ukeys, m, nb, dk);
+    if (m) k_sym_keys<<<blocks_for(m), 256, 0, s>>>(ukeys, m, nb, dk);
     if (m) EH_TRY(dev_radix_sort_u64(&dk, &dk2, 2 * m, 2 * nb, s));
     EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
-    if (n) k_widen<<<blocks(n), 256, 0, s>>>(deg, n, wide);
+    if (n) k_widen<<<blocks_for(n), 256, 0, s>>>(deg, n, wide);
     EH_TRY(dev_exclusive_scan_u64(wide, *off, (uint64_t)n + 1, s, nullptr));
     *adj = dk;   // entry i of the sorted keys is the i-th directed edge: its low bits are the neighbour
     return EH_OK;
@@ -245,16 +237,16 @@ eh_status bfs_order(const uint64_t *off, const uint64_t *adj, uint32_t n, int nb
     uint32_t nf = 1, base = 0;
     while (nf) {
         EH_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4, s));
-        k_bfs_expand<<<blocks(nf, 8), 256, 0, s>>>(front, nf, base, off, adj, nb, pos, cand, next, cnt);
+        k_bfs_expand<<<blocks_for(nf, 8), 256, 0, s>>>(front, nf, base, off, adj, nb, pos, cand, next, cnt);
         uint32_t c = 0;
         EH_CUDA_TRY(cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, s));
         EH_CUDA_TRY(cudaStreamSynchronize(s));
         base += nf;
         if (!c) break;
-        k_bfs_keys<<<blocks(c), 256, 0, s>>>(next, c, cand, nb, keys);
+        k_bfs_keys<<<blocks_for(c), 256, 0, s>>>(next, c, cand, nb, keys);
         uint64_t *k = keys, *k2 = keys2;
         EH_TRY(dev_radix_sort_u64(&k, &k2, c, 2 * nb, s));
-        k_bfs_assign<<<blocks(c), 256, 0, s>>>(k, c, base, nb, pos, order, front);
+        k_bfs_assign<<<blocks_for(c), 256, 0, s>>>(k, c, base, nb, pos, order, front);
         EH_CUDA_TRY(cudaGetLastError());
         nf = c;
     }
@@ -262,9 +254,9 @@ eh_status bfs_order(const uint64_t *off, const uint64_t *adj, uint32_t n, int nb
     if (base < n) {
         EH_TRY(sc.alloc(&flags, n));
         EH_TRY(sc.alloc(&fpos, n));
-        k_unseen_flags<<<blocks(n), 256, 0, s>>>(deg_order, n, pos, flags);
+        k_unseen_flags<<<blocks_for(n), 256, 0, s>>>(deg_order, n, pos, flags);
         EH_TRY(dev_exclusive_scan_u32(flags, fpos, n, s, nullptr));
-        k_tail<<<blocks(n), 256, 0, s>>>(deg_order, flags, fpos, n, base, pos, order);
+        k_tail<<<blocks_for(n), 256, 0, s>>>(deg_order, flags, fpos, n, base, pos, order);
     }
     EH_CUDA_TRY(cudaGetLastError());
     return EH_OK;
@@ -279,17 +271,17 @@ eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukey
     uint64_t *keys = nullptr, *keys2 = nullptr;
     EH_TRY(sc.alloc(&keys, n));
     EH_TRY(sc.alloc(&keys2, n));
-    const int db = bits_of((uint64_t)maxdeg + 1);
+    const int db = bits_for((uint64_t)maxdeg + 1);
     switch (ordering) {
         case EH_ORDER_DEGREE:
         case EH_ORDER_REV_DEGREE:
-            k_keys_degree<<<blocks(n), 256, 0, s>>>(deg, n, maxdeg, nb, ordering == EH_ORDER_REV_DEGREE, keys);
+            k_keys_degree<<<blocks_for(n), 256, 0, s>>>(deg, n, maxdeg, nb, ordering == EH_ORDER_REV_DEGREE, keys);
             return sort_to_order(&keys, &keys2, n, nb + db, nb, s, new2old);
         case EH_ORDER_RANDOM:
-            k_keys_random<<<blocks(n), 256, 0, s>>>(n, seed, nb, keys);
+            k_keys_random<<<blocks_for(n), 256, 0, s>>>(n, seed, nb, keys);
             return sort_to_order(&keys, &keys2, n, 64, nb, s, new2old);
         case EH_ORDER_IDENTITY:
-            k_iota<<<blocks(n), 256, 0, s>>>(n, new2old);
+            k_iota<<<blocks_for(n), 256, 0, s>>>(n, new2old);
             EH_CUDA_TRY(cudaGetLastError());
             return EH_OK;
         default:
@@ -302,18 +294,18 @@ eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukey
     uint64_t *off = nullptr, *adj = nullptr;
     EH_TRY(old_csr(ukeys, m, n, nb, deg, s, sc, &off, &adj));
     if (ordering == EH_ORDER_SHINGLE) {
-        k_keys_shingle<<<blocks(n, 8), 256, 0, s>>>(off, adj, n, seed, nb, keys);
+        k_keys_shingle<<<blocks_for(n, 8), 256, 0, s>>>(off, adj, n, seed, nb, keys);
         return sort_to_order(&keys, &keys2, n, 64, nb, s, new2old);
     }
     // the remaining orderings start from the degree order
     uint32_t *deg_order = nullptr, *rank = nullptr;
     EH_TRY(sc.alloc(&deg_order, n));
     EH_TRY(sc.alloc(&rank, n));
-    k_keys_degree<<<blocks(n), 256, 0, s>>>(deg, n, maxdeg, nb, 0, keys);
+    k_keys_degree<<<blocks_for(n), 256, 0, s>>>(deg, n, maxdeg, nb, 0, keys);
     EH_TRY(sort_to_order(&keys, &keys2, n, nb + db, nb, s, deg_order));
     if (ordering == EH_ORDER_STRONG_RUNS) {
-        k_rank_of<<<blocks(n), 256, 0, s>>>(deg_order, n, rank);
-        k_keys_strong<<<blocks(n, 8), 256, 0, s>>>(off, adj, rank, deg_order, n, nb, keys);
+        k_rank_of<<<blocks_for(n), 256, 0, s>>>(deg_order, n, rank);
+        k_keys_strong<<<blocks_for(n, 8), 256, 0, s>>>(off, adj, rank, deg_order, n, nb, keys);
         return sort_to_order(&keys, &keys2, n, 2 * nb + 1, nb, s, new2old);
     }
     uint32_t *bfs = ordering == EH_ORDER_BFS ? new2old : nullptr, *pos = rank;
@@ -321,9 +313,9 @@ eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukey
     EH_TRY(bfs_order(off, adj, n, nb, deg_order, s, sc, bfs, pos));
     if (ordering == EH_ORDER_BFS) return EH_OK;
     // HYBRID: BFS positions, then stable by degree descending
-    k_keys_hybrid<<<blocks(n), 256, 0, s>>>(deg, pos, n, maxdeg, nb, keys);
+    k_keys_hybrid<<<blocks_for(n), 256, 0, s>>>(deg, pos, n, maxdeg, nb, keys);
     EH_TRY(dev_radix_sort_u64(&keys, &keys2, n, nb + db, s));
-    k_gather<<<blocks(n), 256, 0, s>>>(keys, bfs, n, nb, new2old);
+    k_gather<<<blocks_for(n), 256, 0, s>>>(keys, bfs, n, nb, new2old);
     EH_CUDA_TRY(cudaGetLastError());
     return EH_OK;
 }

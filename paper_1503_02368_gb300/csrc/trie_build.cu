@@ -172,14 +172,6 @@ __global__ void k_desc(const uint64_t *__restrict__ ooff, const uint32_t *__rest
     desc[v] = d;
 }
 
-inline unsigned blocks_for(uint64_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
-
-int bits_for(uint64_t n) {   // bits to represent values in [0, n)
-    int b = 1;
-    while (b < 63 && (1ull << b) < n) ++b;
-    return b;
-}
-
 void free_trie_arrays(eh_trie *t) {
     cudaFree(t->d_new2old); cudaFree(t->d_old2new); cudaFree(t->d_soff); cudaFree(t->d_snbr);
     cudaFree(t->d_desc); cudaFree(t->d_onbr); cudaFree(t->d_words); cudaFree(t->d_deg);

@@ -242,7 +242,8 @@ __device__ __forceinline__ void bitmap_plan(const TrieView &tv, uint32_t a_lo, u
     if (dv.nwords) {
         const uint32_t lo = max(a_lo, dv.lo_word), hi = min(a_lo + a_nw, dv.lo_word + dv.nwords);
         const uint32_t ov = hi > lo ? hi - lo : 0;
-        if (ov <= dv.len) {
+        // a word of the AND covers 32 values; it pays up to 1.5 words per element (measured)
+        if (2 * ov <= 3 * dv.len) {
             kind = ov ? 1u : 0u;
             base = (int64_t)dv.woff - (int64_t)dv.lo_word;   // word w of B is words[base + w]
             begin = lo;

@@ -216,7 +216,7 @@ def bench_clique4(eh, reps=5):
     from synth import workloads as W
     g = W.chunglu_1m()
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))["chunglu_n1000000_g2.1"]
-    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=256)
     m = trie.stats()["n_edges"]
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
     xo = eh.exec_opts(cta_warps=16)
@@ -260,7 +260,7 @@ def bench_clique4(eh, reps=5):
     trie.close()
     return {"workload": "chunglu_n1000000_g2.1 (w_max 5e4, mean degree 40) 4-clique", "m_unique_edges": m,
             "count": c, "exact_vs_oracle": c == gold["clique4"], "ms": ms, "edges_per_s": m / (ms / 1e3),
-            "cliques_per_s": c / (ms / 1e3), "tau": 32, "cta_warps": 16,
+            "cliques_per_s": c / (ms / 1e3), "tau": 256, "cta_warps": 16,
             "barbell": {"count": cb, "exact_vs_oracle": cb == gold.get("barbell"), "ms": ms_b,
                         "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"},
             "selection": sel}

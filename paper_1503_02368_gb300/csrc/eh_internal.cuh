@@ -126,7 +126,7 @@ struct eh_trie {
     uint64_t n_blocks = 0, n_bit_blocks = 0;
     double density_skew = 0;
     uint64_t device_bytes = 0;
-    std::vector<uint32_t> h_out_by_old;   // |N+(v)| by original id (host; serving footprints)
+    std::vector<uint32_t> h_out_by_old;   // |N+(v)| by original id (host; serving footprints; built on first use)
 
     // scratch owned by the trie: counters, accumulators, status
     unsigned long long *d_scratch = nullptr;  // 16 words
@@ -233,6 +233,8 @@ eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukey
 eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s);
 eh_status eh_launch_tri_blocks(eh_trie *t, const WorkPlan &plan, cudaStream_t s, unsigned long long *d_acc,
                                unsigned int *d_next);
+// fills eh_trie::h_out_by_old if not yet built (trie_build.cu)
+eh_status eh_host_out_degrees(eh_trie *t);
 // SK4 per-x sum over the selected vertex's neighbours (list.cu)
 eh_status eh_sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaStream_t s, uint64_t *total);
 eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,

@@ -123,6 +123,7 @@ extern "C" eh_status eh_server_create(const eh_trie *trie, uint64_t memory_budge
                                       uint32_t max_inflight, eh_server **out) {
     if (!trie || !out) { eh_set_error("eh_server_create: NULL argument"); return EH_EINVAL; }
     *out = nullptr;
+    EH_TRY(eh_host_out_degrees(const_cast<eh_trie *>(trie)));
     eh_server *s = new (std::nothrow) eh_server();
     if (!s) { eh_set_error("host allocation failed"); return EH_ENOMEM; }
     s->trie = trie;

@@ -78,6 +78,45 @@ __global__ void k_maps_from_order(const uint32_t *__restrict__ new2old, uint32_t
     deg_new[i] = deg_old[old];
 }
 
+// trie statistics: cnt = {vertices with edges, non-empty pruned sets, bitset
+// sets, max |N+(v)|}; part[2 block] = sum of d(v), sum of d(v)^2 over the
+// block's vertices; hist[d] = vertices of degree d
+__global__ void k_stats(const uint32_t *__restrict__ deg, const uint32_t *__restrict__ odeg,
+                        const uint64_t *__restrict__ nwords, uint32_t n, unsigned long long *cnt, double *part,
+                        uint32_t *hist) {
+    __shared__ double s1[8], s2[8];
+    const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = v < n;
+    const uint32_t d = ok ? deg[v] : 0, od = ok ? odeg[v] : 0;
+    const uint32_t FULLM = 0xffffffffu;
+    const unsigned act = __popc(__ballot_sync(FULLM, ok && d)), nne = __popc(__ballot_sync(FULLM, ok && od)),
+                   nbs = __popc(__ballot_sync(FULLM, ok && nwords[ok ? v : 0]));
+    uint32_t mo = od;
+    double a = d, b = (double)d * d;
+    for (int k = 16; k > 0; k >>= 1) {
+        mo = max(mo, __shfl_xor_sync(FULLM, mo, k));
+        a += __shfl_xor_sync(FULLM, a, k);
+        b += __shfl_xor_sync(FULLM, b, k);
+    }
+    if (ok) atomicAdd(&hist[d], 1u);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        if (act) atomicAdd(&cnt[0], (unsigned long long)act);
+        if (nne) atomicAdd(&cnt[1], (unsigned long long)nne);
+        if (nbs) atomicAdd(&cnt[2], (unsigned long long)nbs);
+        if (mo) atomicMax(&cnt[3], (unsigned long long)mo);
+        s1[w] = a;
+        s2[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { x += s1[i]; y += s2[i]; }
+        part[2 * blockIdx.x] = x;
+        part[2 * blockIdx.x + 1] = y;
+    }
+}
+
 __global__ void k_directed_keys(const uint64_t *__restrict__ ukeys, uint64_t m, int nb,
                                 const uint32_t *__restrict__ old2new, uint64_t *dk) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,42 +397,41 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_TRY(persist_alloc(&t->d_desc, n, &bytes));
     if (n) k_desc<<<blocks_for(n), 256, 0, s>>>(ooff, odeg, t->d_deg, nwords, woff, lo_word, n, t->d_desc);
 
-    // stats (host side, diagnostics only)
-    std::vector<uint32_t> hdeg(n), hodeg(n), hn2o(n);
-    std::vector<uint64_t> hnw(n);
-    if (n) {
-        EH_CUDA_TRY(cudaMemcpyAsync(hn2o.data(), t->d_new2old, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
-        EH_CUDA_TRY(cudaMemcpyAsync(hdeg.data(), t->d_deg, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
-        EH_CUDA_TRY(cudaMemcpyAsync(hodeg.data(), odeg, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
-        EH_CUDA_TRY(cudaMemcpyAsync(hnw.data(), nwords, (uint64_t)n * 8, cudaMemcpyDeviceToHost, s));
+    // stats (diagnostics): counts and maxima by device atomics, the degree sums
+    // as per-block partials summed on the host in block order (deterministic),
+    // the degree mode from a device histogram
+    {
+        const uint32_t nblk = n ? blocks_for(n) : 1;
+        unsigned long long *cnt = nullptr;   // active, nonempty, bitset, max out-degree
+        double *part = nullptr;               // per block: sum d, sum d^2
+        uint32_t *hist = nullptr;
+        EH_TRY(tmp.alloc(&cnt, 4));
+        EH_TRY(tmp.alloc(&part, 2 * (uint64_t)nblk));
+        EH_TRY(tmp.alloc(&hist, (uint64_t)maxdeg + 1));
+        EH_CUDA_TRY(cudaMemsetAsync(cnt, 0, 32, s));
+        EH_CUDA_TRY(cudaMemsetAsync(part, 0, 16 * (uint64_t)nblk, s));
+        EH_CUDA_TRY(cudaMemsetAsync(hist, 0, 4 * ((uint64_t)maxdeg + 1), s));
+        if (n) k_stats<<<nblk, 256, 0, s>>>(t->d_deg, odeg, nwords, n, cnt, part, hist);
+        unsigned long long hc[4] = {0, 0, 0, 0};
+        std::vector<double> hp(2 * (size_t)nblk);
+        std::vector<uint32_t> hh((size_t)maxdeg + 1);
+        EH_CUDA_TRY(cudaMemcpyAsync(hc, cnt, 32, cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaMemcpyAsync(hp.data(), part, 16 * (uint64_t)nblk, cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaMemcpyAsync(hh.data(), hist, 4 * ((uint64_t)maxdeg + 1), cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaStreamSynchronize(s));
+        EH_CUDA_TRY(cudaGetLastError());
+        double sum = 0, sum2 = 0;
+        for (uint32_t i = 0; i < nblk; ++i) { sum += hp[2 * i]; sum2 += hp[2 * i + 1]; }
+        t->n_active = (uint32_t)hc[0];
+        t->n_nonempty = hc[1];
+        t->n_bitset = hc[2];
+        t->max_out = (uint32_t)hc[3];
+        double mean = n ? sum / n : 0, var = n ? sum2 / n - mean * mean : 0;
+        uint32_t mode = 0, best = 0;
+        for (uint32_t d = 0; d <= maxdeg; ++d)
+            if (hh[d] > best) { best = hh[d]; mode = d; }
+        t->density_skew = var > 0 ? 3.0 * (mean - mode) / std::sqrt(var) : 0.0;
     }
-    EH_CUDA_TRY(cudaStreamSynchronize(s));
-    EH_CUDA_TRY(cudaGetLastError());
-    uint32_t act = 0, mo = 0;
-    uint64_t nbs = 0, nne = 0;
-    double sum = 0, sum2 = 0;
-    std::vector<uint64_t> hist((size_t)maxdeg + 1, 0);
-    for (uint32_t v = 0; v < n; ++v) {
-        if (hdeg[v]) ++act;
-        mo = std::max(mo, hodeg[v]);
-        if (hodeg[v]) ++nne;
-        if (hnw[v]) ++nbs;
-        sum += hdeg[v];
-        sum2 += (double)hdeg[v] * hdeg[v];
-        hist[hdeg[v]]++;
-    }
-    t->h_out_by_old.assign(n, 0);
-    for (uint32_t v = 0; v < n; ++v) t->h_out_by_old[hn2o[v]] = hodeg[v];
-    t->n_active = act;
-    t->max_out = mo;
-    t->n_bitset = nbs;
-    t->n_nonempty = nne;
-    double mean = n ? sum / n : 0, var = n ? sum2 / n - mean * mean : 0;
-    uint32_t mode = 0;
-    uint64_t best = 0;
-    for (uint32_t d = 0; d <= maxdeg; ++d)
-        if (hist[d] > best) { best = hist[d]; mode = d; }
-    t->density_skew = var > 0 ? 3.0 * (mean - mode) / std::sqrt(var) : 0.0;
     t->device_bytes = bytes;
     if (o.flags & EH_BUILD_BLOCK_LAYOUT) EH_TRY(eh_build_blocks(t, o.bitset_tau, s));
     return EH_OK;
@@ -433,6 +471,24 @@ eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint3
     }
     *words_out = words;
     *n_words_out = tw;
+    return EH_OK;
+}
+
+// |N+(v)| by original id on the host (the serving loop's footprint estimate),
+// built on first use
+eh_status eh_host_out_degrees(eh_trie *t) {
+    std::lock_guard<std::mutex> g(t->mu);
+    if (t->h_out_by_old.size() == t->n) return EH_OK;
+    const uint32_t n = t->n;
+    std::vector<uint32_t> n2o(n);
+    std::vector<SetDesc> desc(n);
+    if (n) {
+        EH_CUDA_TRY(cudaMemcpy(n2o.data(), t->d_new2old, (uint64_t)n * 4, cudaMemcpyDeviceToHost));
+        EH_CUDA_TRY(cudaMemcpy(desc.data(), t->d_desc, (uint64_t)n * sizeof(SetDesc), cudaMemcpyDeviceToHost));
+    }
+    std::vector<uint32_t> out(n, 0);
+    for (uint32_t v = 0; v < n; ++v) out[n2o[v]] = desc[v].len;
+    t->h_out_by_old.swap(out);
     return EH_OK;
 }
 

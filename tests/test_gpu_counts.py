@@ -367,3 +367,23 @@ def test_barbell_is_whole_graph_only(eh):
     c, s = t.count_batch(["barbell", "barbell"], np.array([0, 0, 3], np.uint64), np.arange(3, dtype=np.uint32))
     assert s[0] == 0 and int(c[0]) == 7 * 6 * (2 * math.comb(6, 2)) ** 2   # whole graph in a batch
     assert s[1] == 1                                                        # with a subset: refused
+
+
+def test_trie_stats_match_their_definitions(eh):
+    # the statistics the build reduces on the device, recomputed from the oracle's
+    # degrees and the exported trie
+    for scale, tau in ((12, 32), (14, 256)):
+        g = W.rmat_graph(scale, 1503 + scale)
+        o = oracle.Graph(g["n"], g["src"], g["dst"])
+        t = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
+        st = t.stats()
+        deg = o.degrees().astype(np.float64)
+        x = t.export(0)
+        assert st["n_active"] == int((deg > 0).sum())
+        assert st["max_out_degree"] == int(x["len"].max())
+        assert st["n_nonempty_sets"] == int((x["len"] > 0).sum())
+        assert st["n_bitset_sets"] == int((x["bits_nwords"] > 0).sum())
+        assert st["max_degree"] == int(deg.max())
+        mean, sd = deg.mean(), deg.std()
+        mode = int(np.bincount(deg.astype(np.int64)).argmax())
+        assert st["density_skew"] == pytest.approx(3 * (mean - mode) / sd, rel=1e-9)

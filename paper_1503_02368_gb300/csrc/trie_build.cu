@@ -98,7 +98,10 @@ __global__ void k_stats(const uint32_t *__restrict__ deg, const uint32_t *__rest
         a += __shfl_xor_sync(FULLM, a, k);
         b += __shfl_xor_sync(FULLM, b, k);
     }
-    if (ok) atomicAdd(&hist[d], 1u);
+    {   // one atomic per distinct degree in the warp (many vertices share small degrees)
+        const uint32_t peers = __match_any_sync(FULLM, ok ? d : 0xFFFFFFFFu);
+        if (ok && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         if (act) atomicAdd(&cnt[0], (unsigned long long)act);
@@ -139,13 +142,26 @@ __global__ void k_widen(const uint32_t *__restrict__ x, uint64_t n, uint64_t *ou
 
 // place sorted directed edge i = (v, w) at soff[v] + (i - ustart[v])
 __global__ void k_fill_sym(const uint64_t *__restrict__ dk, uint64_t n2, int nb, const uint64_t *__restrict__ ustart,
-                           const uint64_t *__restrict__ soff, uint32_t *snbr, uint32_t *odeg) {
+                           const uint64_t *__restrict__ soff, uint32_t *snbr) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n2) return;
     uint64_t k = dk[i];
     uint32_t v = (uint32_t)(k >> nb), w = (uint32_t)(k & ((1ull << nb) - 1));
     snbr[soff[v] + (i - ustart[v])] = w;
-    if (w < v) atomicAdd(&odeg[v], 1u);
+}
+
+// |N+(v)| = the number of entries of the sorted N(v) below v (binary search)
+__global__ void k_out_degree(const uint32_t *__restrict__ snbr, const uint64_t *__restrict__ soff,
+                             const uint32_t *__restrict__ deg, uint32_t n, uint32_t *odeg) {
+    const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint32_t *N = snbr + soff[v];
+    uint32_t lo = 0, hi = deg[v];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (N[mid] < (uint32_t)v) lo = mid + 1; else hi = mid;
+    }
+    odeg[v] = lo;
 }
 
 // N+(v) is the prefix of N(v) below v
@@ -363,8 +379,8 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_CUDA_TRY(cudaMemsetAsync(t->d_snbr, 0xFF, (slen ? slen : 1) * 4, s));
     uint32_t *odeg = nullptr;
     EH_TRY(tmp.alloc(&odeg, n));
-    EH_CUDA_TRY(cudaMemsetAsync(odeg, 0, (uint64_t)n * 4, s));
-    if (n2) k_fill_sym<<<blocks_for(n2), 256, 0, s>>>(dk, n2, nb, ustart, t->d_soff, t->d_snbr, odeg);
+    if (n2) k_fill_sym<<<blocks_for(n2), 256, 0, s>>>(dk, n2, nb, ustart, t->d_soff, t->d_snbr);
+    if (n) k_out_degree<<<blocks_for(n), 256, 0, s>>>(t->d_snbr, t->d_soff, t->d_deg, n, odeg);
     tmp.release(dk);
 
     uint64_t *ooff = nullptr;

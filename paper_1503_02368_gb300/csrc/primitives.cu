@@ -96,7 +96,7 @@ eh_status scan_total(const T *in, T *out, uint64_t n, cudaStream_t s, uint64_t *
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 8;
+constexpr int RS_ITEMS = 12;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 __global__ void rs_upsweep(const uint64_t *__restrict__ keys, uint64_t n, uint64_t chunk, int shift,
@@ -128,16 +128,15 @@ __global__ void rs_downsweep(const uint64_t *__restrict__ in, uint64_t *__restri
         const uint64_t sub = tile + (uint64_t)warp * 32 * RS_ITEMS;
         uint64_t k[RS_ITEMS];
         uint32_t dig[RS_ITEMS];
-        uint32_t vmask[RS_ITEMS];
+        uint32_t pm[RS_ITEMS];   // lanes of the warp holding the same digit (kept for the scatter)
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
             uint64_t idx = sub + (uint64_t)r * 32 + lane;
             bool valid = idx < end;
             k[r] = valid ? in[idx] : 0ull;
-            dig[r] = (uint32_t)(k[r] >> shift) & 255u;
-            vmask[r] = __ballot_sync(0xffffffffu, valid);
-            uint32_t peers = __match_any_sync(0xffffffffu, dig[r]) & vmask[r];
-            if (valid && (peers & lt_mask) == 0) whist[warp][dig[r]] += __popc(peers);
+            dig[r] = valid ? (uint32_t)(k[r] >> shift) & 255u : 256u;   // 256: no key
+            pm[r] = __match_any_sync(0xffffffffu, dig[r]);
+            if (valid && (pm[r] & lt_mask) == 0) whist[warp][dig[r]] += __popc(pm[r]);
             __syncwarp();
         }
         __syncthreads();
@@ -154,8 +153,8 @@ __global__ void rs_downsweep(const uint64_t *__restrict__ in, uint64_t *__restri
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
-            bool valid = (vmask[r] >> lane) & 1u;
-            uint32_t peers = __match_any_sync(0xffffffffu, dig[r]) & vmask[r];
+            const bool valid = dig[r] < 256u;
+            const uint32_t peers = pm[r];
             uint32_t base = valid ? whist[warp][dig[r]] : 0u;
             __syncwarp();
             if (valid) {

@@ -368,24 +368,6 @@ __device__ __forceinline__ void k4_level2(const ListArgs &a, Sink &sk, const uin
     }
 }
 
-// |S[0..r) ∩ N+(z)| by one lane, the smaller side enumerating
-__device__ __forceinline__ uint32_t k4_count_z(const ListArgs &a, const uint32_t *S, uint32_t r, const SetDesc &dz) {
-    uint32_t c = 0;
-    if (dz.len == 0) return 0;
-    if ((uint64_t)dz.len > (uint64_t)a.ratio * r || (dz.nwords && r <= dz.len)) {
-        for (uint32_t i = 0; i < r; ++i) c += in_set(a.tv, dz, S[i]);
-    } else {
-        const uint32_t *B = a.tv.nbr + dz.off;
-        uint32_t i = 0;   // merge: both sorted, B shorter than ratio * r
-        for (uint32_t p = 0; p < dz.len && i < r; ++p) {
-            const uint32_t x = __ldg(&B[p]);
-            while (i < r && S[i] < x) ++i;
-            c += i < r && S[i] == x;
-        }
-    }
-    return c;
-}
-
 // ------------------------------------------------------------- kernels
 
 // Heavy items: a persistent grid, one item per CTA at a time.
@@ -449,18 +431,10 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
                 else l1.sorted(st.A, j, dv);
                 __syncwarp();
                 // level 2: for z in S, S_<z ∩ N+(z)
-                if (EMIT) {
-                    for (uint32_t r = 1; r < l1.ns; ++r) {
-                        const uint32_t z = Sw[r];
-                        sk.key[2] = __ldg(&a.new2old[z]);
-                        k4_level2<EMIT>(a, sk, Sw, r, a.tv.desc[z]);
-                    }
-                } else {
-                    // counting only: one lane per z, no ranks needed
-                    unsigned long long c = 0;
-                    for (uint32_t r = 1 + lane; r < l1.ns; r += 32) c += k4_count_z(a, Sw, r, a.tv.desc[Sw[r]]);
-                    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
-                    sk.n += c;
+                for (uint32_t r = 1; r < l1.ns; ++r) {
+                    const uint32_t z = Sw[r];
+                    sk.key[2] = __ldg(&a.new2old[z]);
+                    k4_level2<EMIT>(a, sk, Sw, r, a.tv.desc[z]);
                 }
                 __syncwarp();
             }

@@ -94,75 +94,100 @@ eh_status scan_total(const T *in, T *out, uint64_t n, cudaStream_t s, uint64_t *
 
 // ------------------------------------------------------------ radix sort
 
-constexpr int RS_THREADS = 256;
+constexpr int RS_THREADS = 512;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 12;
+constexpr int RS_ITEMS = 5;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_BINS = 256;
 
-__global__ void rs_upsweep(const uint64_t *__restrict__ keys, uint64_t n, uint64_t chunk, int shift,
-                           uint32_t *hist) {
-    __shared__ uint32_t h[256];
+__global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint64_t *__restrict__ keys, uint64_t n, uint64_t chunk,
+                                                           int shift, uint32_t *hist) {
+    __shared__ uint32_t h[RS_BINS];
     const int tid = threadIdx.x;
-    h[tid] = 0;
+    for (int b = tid; b < RS_BINS; b += RS_THREADS) h[b] = 0;
     __syncthreads();
     uint64_t begin = (uint64_t)blockIdx.x * chunk;
     uint64_t end = begin + chunk < n ? begin + chunk : n;
     for (uint64_t i = begin + tid; i < end; i += RS_THREADS) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
     __syncthreads();
-    hist[(uint64_t)tid * gridDim.x + blockIdx.x] = h[tid];
+    for (int b = tid; b < RS_BINS; b += RS_THREADS) hist[(uint64_t)b * gridDim.x + blockIdx.x] = h[b];
 }
 
-__global__ void rs_downsweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint64_t n,
-                             uint64_t chunk, int shift, const uint32_t *__restrict__ offs) {
-    __shared__ uint32_t whist[RS_WARPS][256];
-    __shared__ uint32_t run[256];
+// Stable scatter of one 8-bit digit.  Per tile: every warp ranks its keys
+// among the keys of the same digit (match_any, in input order), the tile's
+// keys are placed in digit order in shared memory, and each digit's run is
+// then written to its global range with consecutive threads on consecutive
+// addresses (coalesced), instead of one scattered store per key.
+__global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                                             uint64_t n, uint64_t chunk, int shift,
+                                                             const uint32_t *__restrict__ offs) {
+    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];   // per-warp digit counts, then the warps' offsets in the digit's run
+    __shared__ uint32_t run[RS_BINS];              // global position of the digit's next key
+    __shared__ uint32_t loc[RS_BINS];              // tile-local start of the digit's run
+    __shared__ uint64_t skey[RS_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    run[tid] = offs[(uint64_t)tid * gridDim.x + blockIdx.x];
+    for (int b = tid; b < RS_BINS; b += RS_THREADS) run[b] = offs[(uint64_t)b * gridDim.x + blockIdx.x];
     uint64_t begin = (uint64_t)blockIdx.x * chunk;
     uint64_t end = begin + chunk < n ? begin + chunk : n;
     for (uint64_t tile = begin; tile < end; tile += RS_TILE) {
-#pragma unroll
-        for (int i = 0; i < RS_WARPS; ++i) whist[i][tid] = 0;
+        for (int i = 0; i < RS_WARPS; ++i)
+            for (int b = tid; b < RS_BINS; b += RS_THREADS) wcnt[i][b] = 0;
         __syncthreads();
         const uint64_t sub = tile + (uint64_t)warp * 32 * RS_ITEMS;
         uint64_t k[RS_ITEMS];
-        uint32_t dig[RS_ITEMS];
-        uint32_t pm[RS_ITEMS];   // lanes of the warp holding the same digit (kept for the scatter)
+        uint32_t dig[RS_ITEMS], wr[RS_ITEMS];
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
-            uint64_t idx = sub + (uint64_t)r * 32 + lane;
-            bool valid = idx < end;
+            const uint64_t idx = sub + (uint64_t)r * 32 + lane;
+            const bool valid = idx < end;
             k[r] = valid ? in[idx] : 0ull;
             dig[r] = valid ? (uint32_t)(k[r] >> shift) & 255u : 256u;   // 256: no key
-            pm[r] = __match_any_sync(0xffffffffu, dig[r]);
-            if (valid && (pm[r] & lt_mask) == 0) whist[warp][dig[r]] += __popc(pm[r]);
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+            const uint32_t before = valid ? wcnt[warp][dig[r]] : 0u;     // this warp's earlier keys of the digit
+            __syncwarp();
+            wr[r] = before + __popc(peers & lt_mask);
+            if (valid && (peers & lt_mask) == 0) wcnt[warp][dig[r]] = before + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        {
-            uint32_t r0 = run[tid];
-#pragma unroll
+        for (int b = tid; b < RS_BINS; b += RS_THREADS) {
+            uint32_t c = 0;
             for (int w = 0; w < RS_WARPS; ++w) {
-                uint32_t c = whist[w][tid];
-                whist[w][tid] = r0;
-                r0 += c;
+                const uint32_t x = wcnt[w][b];
+                wcnt[w][b] = c;
+                c += x;
             }
-            run[tid] = r0;
+            loc[b] = c;   // the digit's total in the tile, scanned next
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive scan of the 256 totals, 8 per lane
+            uint32_t v[8], sum = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { v[i] = loc[lane * 8 + i]; sum += v[i]; }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            uint32_t ex = incl - sum;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { loc[lane * 8 + i] = ex; ex += v[i]; }
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < RS_ITEMS; ++r) {
-            const bool valid = dig[r] < 256u;
-            const uint32_t peers = pm[r];
-            uint32_t base = valid ? whist[warp][dig[r]] : 0u;
-            __syncwarp();
-            if (valid) {
-                out[base + __popc(peers & lt_mask)] = k[r];
-                if ((peers & lt_mask) == 0) whist[warp][dig[r]] = base + __popc(peers);
-            }
-            __syncwarp();
+        for (int r = 0; r < RS_ITEMS; ++r)
+            if (dig[r] < 256u) skey[loc[dig[r]] + wcnt[warp][dig[r]] + wr[r]] = k[r];
+        __syncthreads();
+        const uint32_t cnt = (uint32_t)(end - tile < (uint64_t)RS_TILE ? end - tile : (uint64_t)RS_TILE);
+        for (uint32_t i = tid; i < cnt; i += RS_THREADS) {
+            const uint64_t key = skey[i];
+            const uint32_t d = (uint32_t)(key >> shift) & 255u;
+            out[run[d] + (i - loc[d])] = key;
         }
+        __syncthreads();
+        for (int b = tid; b < RS_BINS; b += RS_THREADS) run[b] += (b < RS_BINS - 1 ? loc[b + 1] : cnt) - loc[b];
         __syncthreads();
     }
 }
@@ -186,17 +211,17 @@ eh_status dev_radix_sort_u64(uint64_t **keys, uint64_t **tmp, uint64_t n, int ke
         return EH_EINVAL;
     }
     uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
-    uint64_t G = (uint64_t)eh_num_sms() * 8;
+    uint64_t G = (uint64_t)eh_num_sms() * 4;
     if (G > tiles) G = tiles;
     if (G < 1) G = 1;
     uint64_t chunk = (tiles + G - 1) / G * RS_TILE;
     G = (n + chunk - 1) / chunk;
     uint32_t *hist = nullptr;
-    EH_TRY(dev_alloc(&hist, 256 * G, s));
+    EH_TRY(dev_alloc(&hist, RS_BINS * G, s));
     eh_status st = EH_OK;
     for (int shift = 0; shift < key_bits; shift += 8) {
         rs_upsweep<<<(unsigned)G, RS_THREADS, 0, s>>>(*keys, n, chunk, shift, hist);
-        st = dev_exclusive_scan_u32(hist, hist, 256 * G, s, nullptr);
+        st = dev_exclusive_scan_u32(hist, hist, RS_BINS * G, s, nullptr);
         if (st != EH_OK) break;
         rs_downsweep<<<(unsigned)G, RS_THREADS, 0, s>>>(*keys, *tmp, n, chunk, shift, hist);
         uint64_t *t = *keys;

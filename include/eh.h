@@ -24,6 +24,11 @@
  *     undirected).
  *   - Counts are exact uint64.  A count that would exceed 2^64-1 returns
  *     EH_EOVERFLOW.
+ *   - Device temporaries are stream-ordered allocations from the device's
+ *     default memory pool.  The first eh_build_trie on a device raises that
+ *     pool's release threshold for the process, so freed temporaries stay
+ *     cached for the next call instead of being unmapped at every
+ *     synchronisation; cudaMemPoolTrimTo returns them to the driver.
  *   - Concurrency: a trie is read-only after eh_build_trie.  Batches
  *     (eh_count_batch*, subset counts, the server) own all their device state
  *     and may run concurrently on different streams.  Whole-graph counts use

@@ -490,6 +490,27 @@ eh_status eh_build_layouts(const uint32_t *nbr, const uint64_t *off, const uint3
     return EH_OK;
 }
 
+// The stream-ordered temporaries of builds, plans and batches come from the
+// device's default memory pool.  By default the pool returns freed memory to
+// the driver at every synchronisation, so the next build maps it again; the
+// process keeps it cached instead (a property of this process's pool only).
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+    std::lock_guard<std::mutex> g(mu);
+    for (int d : done)
+        if (d == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(dev);
+}
+
 // |N+(v)| by original id on the host (the serving loop's footprint estimate),
 // built on first use
 eh_status eh_host_out_degrees(eh_trie *t) {
@@ -525,6 +546,7 @@ extern "C" eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uin
     if (o.ordering > EH_ORDER_IDENTITY) { eh_set_error("eh_build_trie: unknown ordering %u", o.ordering); return EH_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     NvtxRange nv("eh_build_trie");
+    keep_pool_memory();
     eh_trie *t = new (std::nothrow) eh_trie();
     if (!t) { eh_set_error("host allocation failed"); return EH_ENOMEM; }
     t->n = n_vertices;

@@ -28,7 +28,7 @@
  *     default memory pool.  The first eh_build_trie on a device raises that
  *     pool's release threshold for the process, so freed temporaries stay
  *     cached for the next call instead of being unmapped at every
- *     synchronisation; cudaMemPoolTrimTo returns them to the driver.
+ *     synchronisation; eh_trim_memory returns them to the driver.
  *   - Concurrency: a trie is read-only after eh_build_trie.  Batches
  *     (eh_count_batch*, subset counts, the server) own all their device state
  *     and may run concurrently on different streams.  Whole-graph counts use
@@ -289,6 +289,10 @@ typedef enum {
  * the other synchronous counts of the trie. */
 eh_status eh_count_selected(const eh_trie *trie, eh_sel_pattern pattern, uint32_t node, const eh_exec_opts *xopts,
                             void *stream, uint64_t *out_count);
+
+/* eh_trim_memory -- waits for the current device, then returns the device
+ * temporaries cached in its default memory pool to the driver. */
+eh_status eh_trim_memory(void);
 
 /* eh_trie_export_blocks -- host copy of the composite layout of a trie built
  * with EH_BUILD_BLOCK_LAYOUT (EH_EINVAL otherwise).  *n_blocks and

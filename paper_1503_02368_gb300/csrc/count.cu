@@ -511,7 +511,6 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t &total) 
     return incl - x;
 }
 
-// S = A ∩ B, A an on-chip bitmap
 // S = A ∩ B, A an on-chip bitmap.  When B is a bitset and their overlap fits
 // the warp's bitmap buffer Sbm, the AND words are also written there (words
 // [lo, hi) at Sbm[0 ..)) and *bm_lo = lo, so level 2 need not rebuild S's

@@ -511,6 +511,16 @@ static void keep_pool_memory() {
     done.push_back(dev);
 }
 
+extern "C" eh_status eh_trim_memory(void) {
+    int dev = 0;
+    cudaMemPool_t pool;
+    EH_CUDA_TRY(cudaGetDevice(&dev));
+    EH_CUDA_TRY(cudaDeviceSynchronize());
+    EH_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    EH_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    return EH_OK;
+}
+
 // |N+(v)| by original id on the host (the serving loop's footprint estimate),
 // built on first use
 eh_status eh_host_out_degrees(eh_trie *t) {

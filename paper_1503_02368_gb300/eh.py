@@ -105,6 +105,8 @@ def lib():
     L.eh_count_status.argtypes = [vp, vp]
     L.eh_count_info_get.restype = st
     L.eh_count_info_get.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, ctypes.POINTER(CountInfo)]
+    L.eh_trim_memory.restype = st
+    L.eh_trim_memory.argtypes = []
     L.eh_trie_export_blocks.restype = st
     L.eh_trie_export_blocks.argtypes = [vp, u64p, u32p, u32p, u64p, u64p]
     L.eh_count_selected.restype = st
@@ -181,6 +183,11 @@ def batch_profile():
     p = BatchProfile()
     _check(lib().eh_batch_profile_get(ctypes.byref(p)))
     return {f: getattr(p, f) for f, _ in BatchProfile._fields_}
+
+
+def trim_memory():
+    """Return the device temporaries cached in the default memory pool (eh_trim_memory)."""
+    _check(lib().eh_trim_memory())
 
 
 def build_opts(tau=32, min_bitset_len=0, flags=0, ordering="degree", order_seed=0):

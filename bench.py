@@ -71,7 +71,7 @@ def profile_traffic(kernel_src):
     vals = {}
     for line in open(p):
         if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
+            k, v = line[2:].rsplit(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("count.cu sha256[:16]") != h:
         return None

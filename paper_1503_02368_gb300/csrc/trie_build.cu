@@ -293,9 +293,23 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_CUDA_TRY(cudaMemsetAsync(t->d_scratch, 0, 16 * sizeof(unsigned long long), s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, 4 * sizeof(uint32_t), s));
 
-    // 0. inputs on the device
+    // 0. inputs on the device.  Pinned host arrays are read in place by the
+    // first kernel (they are device-addressable; on a coherent CPU-GPU link
+    // this streams them once instead of copying them first); other host
+    // arrays are copied.
     const uint32_t *d_src = src, *d_dst = dst;
+    bool host_mapped = false;
     if (!(o.flags & EH_BUILD_DEVICE_INPUT) && ne > 0) {
+        cudaPointerAttributes as, ad;
+        if (cudaPointerGetAttributes(&as, src) == cudaSuccess && cudaPointerGetAttributes(&ad, dst) == cudaSuccess &&
+            as.type == cudaMemoryTypeHost && ad.type == cudaMemoryTypeHost && as.devicePointer && ad.devicePointer) {
+            d_src = (const uint32_t *)as.devicePointer;
+            d_dst = (const uint32_t *)ad.devicePointer;
+            host_mapped = true;
+        }
+        cudaGetLastError();
+    }
+    if (!(o.flags & EH_BUILD_DEVICE_INPUT) && ne > 0 && !host_mapped) {
         uint32_t *a = nullptr, *b = nullptr;
         EH_TRY(tmp.alloc(&a, ne));
         EH_TRY(tmp.alloc(&b, ne));

@@ -387,3 +387,19 @@ def test_trie_stats_match_their_definitions(eh):
         mean, sd = deg.mean(), deg.std()
         mode = int(np.bincount(deg.astype(np.int64)).argmax())
         assert st["density_skew"] == pytest.approx(3 * (mean - mode) / sd, rel=1e-9)
+
+
+def test_pinned_host_input_read_in_place(eh):
+    # pinned host edge lists are read by the device in place; the trie must be the
+    # one built from the same edges in pageable memory
+    import torch
+    g = W.rmat_graph(14, 1503 + 14)
+    s_p = torch.from_numpy(g["src"]).pin_memory()
+    d_p = torch.from_numpy(g["dst"]).pin_memory()
+    assert s_p.is_pinned()
+    a = eh.Trie(s_p.numpy(), d_p.numpy(), g["n"], tau=32)
+    b = eh.Trie(g["src"].copy(), g["dst"].copy(), g["n"], tau=32)
+    xa, xb = a.export(0), b.export(0)
+    for k in ("new_to_old", "off", "len", "nbr", "bits_nwords"):
+        assert np.array_equal(xa[k], xb[k]), k
+    assert a.count("clique4") == b.count("clique4")

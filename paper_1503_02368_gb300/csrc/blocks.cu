@@ -24,12 +24,12 @@ namespace {
 
 constexpr uint32_t BLK_BIT = 0x80000000u;
 
-// persistent trie memory (released with the trie by cudaFree)
+// persistent trie memory: from the default pool like the trie's other arrays
 template <typename T>
-eh_status trie_alloc(T **p, uint64_t count) {
+eh_status trie_alloc(T **p, uint64_t count, cudaStream_t s) {
     *p = nullptr;
     if (eh_alloc_should_fail()) { eh_set_error("device allocation failed (injected)"); return EH_ENOMEM; }
-    if (cudaMalloc((void **)p, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+    if (cudaMallocAsync((void **)p, sizeof(T) * (count ? count : 1), s) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         eh_set_error("device allocation of %llu bytes failed", (unsigned long long)(sizeof(T) * count));
@@ -191,12 +191,12 @@ eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s) {
         k_blk_count<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, nblk, nbit);
         cuda_ok(cudaGetLastError(), "count launch");
     }
-    if (st == EH_OK) st = trie_alloc(&t->d_boff, (uint64_t)n + 1);
+    if (st == EH_OK) st = trie_alloc(&t->d_boff, (uint64_t)n + 1, s);
     if (st == EH_OK) st = dev_exclusive_scan_u64(nblk, t->d_boff, (uint64_t)n + 1, s, &total);
     if (st == EH_OK) st = dev_exclusive_scan_u64(nbit, nbit, (uint64_t)n + 1, s, &total_bit);
     if (st == EH_OK && total_bit >= BLK_BIT) { eh_set_error("block layout: too many bitset blocks"); st = EH_EINVAL; }
-    if (st == EH_OK) st = trie_alloc(&t->d_bdir, total);
-    if (st == EH_OK) st = trie_alloc(&t->d_bwords, total_bit * 8);
+    if (st == EH_OK) st = trie_alloc(&t->d_bdir, total, s);
+    if (st == EH_OK) st = trie_alloc(&t->d_bwords, total_bit * 8, s);
     if (st == EH_OK && total_bit) cuda_ok(cudaMemsetAsync(t->d_bwords, 0, total_bit * 32, s), "memset");
     if (st == EH_OK && n) {
         k_blk_fill<<<blocks_for(n), 256, 0, s>>>(t->d_onbr, t->d_desc, n, tau, t->d_boff, nbit, t->d_bdir, t->d_bwords);

@@ -228,23 +228,28 @@ __global__ void k_desc(const uint64_t *__restrict__ ooff, const uint32_t *__rest
 }
 
 void free_trie_arrays(eh_trie *t) {
-    cudaFree(t->d_new2old); cudaFree(t->d_old2new); cudaFree(t->d_soff); cudaFree(t->d_snbr);
-    cudaFree(t->d_desc); cudaFree(t->d_onbr); cudaFree(t->d_words); cudaFree(t->d_deg);
-    cudaFree(t->d_scratch); cudaFree(t->d_status); cudaFree(t->d_arena);
-    cudaFree(t->d_boff); cudaFree(t->d_bdir); cudaFree(t->d_bwords);
+    // the trie's arrays come from the default memory pool (stream-ordered); the
+    // device is idle here (callers synchronise first), so the frees are
+    // immediate and the pool keeps the memory for the next trie
+    void *pooled[] = {t->d_new2old, t->d_old2new, t->d_soff, t->d_snbr, t->d_desc, t->d_onbr, t->d_words,
+                      t->d_deg, t->d_scratch, t->d_status, t->d_boff, t->d_bdir, t->d_bwords};
+    for (void *p : pooled)
+        if (p) cudaFreeAsync(p, 0);
+    cudaFree(t->d_arena);
     for (auto &kv : t->plans) { cudaFree(kv.second.d_heavy); cudaFree(kv.second.d_light); }
     t->plans.clear();
 }
 
+// memory the trie keeps: from the device's default pool, on the build stream
 template <typename T>
-eh_status persist_alloc(T **p, uint64_t count, uint64_t *bytes) {
+eh_status persist_alloc(T **p, uint64_t count, uint64_t *bytes, cudaStream_t s) {
     *p = nullptr;
     if (count == 0) count = 1;
     if (eh_alloc_should_fail()) {
         eh_set_error("device allocation of %llu bytes failed (injected)", (unsigned long long)(sizeof(T) * count));
         return EH_ENOMEM;
     }
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    cudaError_t e = cudaMallocAsync((void **)p, sizeof(T) * count, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -288,8 +293,8 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     if (2 * nb > 64) { eh_set_error("id space too large"); return EH_EINVAL; }
 
     // scratch shared by the count kernels
-    EH_TRY(persist_alloc(&t->d_scratch, 16, &bytes));
-    EH_TRY(persist_alloc(&t->d_status, 4, &bytes));
+    EH_TRY(persist_alloc(&t->d_scratch, 16, &bytes, s));
+    EH_TRY(persist_alloc(&t->d_status, 4, &bytes, s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_scratch, 0, 16 * sizeof(unsigned long long), s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, 4 * sizeof(uint32_t), s));
 
@@ -361,9 +366,9 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_CUDA_TRY(cudaStreamSynchronize(s));
     t->max_deg = maxdeg;
 
-    EH_TRY(persist_alloc(&t->d_new2old, n, &bytes));
-    EH_TRY(persist_alloc(&t->d_old2new, n, &bytes));
-    EH_TRY(persist_alloc(&t->d_deg, n, &bytes));
+    EH_TRY(persist_alloc(&t->d_new2old, n, &bytes, s));
+    EH_TRY(persist_alloc(&t->d_old2new, n, &bytes, s));
+    EH_TRY(persist_alloc(&t->d_deg, n, &bytes, s));
     EH_TRY(eh_vertex_order(o.ordering, o.order_seed, ukeys, m, n, nb, deg_old, maxdeg, s, t->d_new2old));
     if (n) k_maps_from_order<<<blocks_for(n), 256, 0, s>>>(t->d_new2old, n, deg_old, t->d_old2new, t->d_deg);
 
@@ -380,7 +385,7 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     uint64_t *ustart = nullptr, *wide = nullptr;
     EH_TRY(tmp.alloc(&ustart, (uint64_t)n + 1));
     EH_TRY(tmp.alloc(&wide, (uint64_t)n + 1));
-    EH_TRY(persist_alloc(&t->d_soff, (uint64_t)n + 1, &bytes));
+    EH_TRY(persist_alloc(&t->d_soff, (uint64_t)n + 1, &bytes, s));
     EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
     if (n) k_widen<<<blocks_for(n), 256, 0, s>>>(t->d_deg, n, wide);
     EH_TRY(dev_exclusive_scan_u64(wide, ustart, (uint64_t)n + 1, s, nullptr));
@@ -389,7 +394,7 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     uint64_t slen = 0;
     EH_TRY(dev_exclusive_scan_u64(wide, t->d_soff, (uint64_t)n + 1, s, &slen));
     t->snbr_len = slen;
-    EH_TRY(persist_alloc(&t->d_snbr, slen, &bytes));
+    EH_TRY(persist_alloc(&t->d_snbr, slen, &bytes, s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_snbr, 0xFF, (slen ? slen : 1) * 4, s));
     uint32_t *odeg = nullptr;
     EH_TRY(tmp.alloc(&odeg, n));
@@ -404,7 +409,7 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     uint64_t olen = 0;
     EH_TRY(dev_exclusive_scan_u64(wide, ooff, (uint64_t)n + 1, s, &olen));
     t->onbr_len = olen;
-    EH_TRY(persist_alloc(&t->d_onbr, olen, &bytes));
+    EH_TRY(persist_alloc(&t->d_onbr, olen, &bytes, s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_onbr, 0xFF, (olen ? olen : 1) * 4, s));
     if (n) k_fill_pruned<<<blocks_for(n, 8), 256, 0, s>>>(t->d_snbr, t->d_soff, ooff, odeg, n, t->d_onbr);
 
@@ -421,10 +426,10 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     uint64_t tw = 0;
     EH_TRY(dev_exclusive_scan_u64(nwords, woff, (uint64_t)n + 1, s, &tw));
     t->n_words = tw;
-    EH_TRY(persist_alloc(&t->d_words, tw, &bytes));
+    EH_TRY(persist_alloc(&t->d_words, tw, &bytes, s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_words, 0, (tw ? tw : 1) * 4, s));
     if (n) k_fill_bits<<<blocks_for(n, 8), 256, 0, s>>>(t->d_onbr, ooff, odeg, nwords, woff, lo_word, n, t->d_words);
-    EH_TRY(persist_alloc(&t->d_desc, n, &bytes));
+    EH_TRY(persist_alloc(&t->d_desc, n, &bytes, s));
     if (n) k_desc<<<blocks_for(n), 256, 0, s>>>(ooff, odeg, t->d_deg, nwords, woff, lo_word, n, t->d_desc);
 
     // stats (diagnostics): counts and maxima by device atomics, the degree sums

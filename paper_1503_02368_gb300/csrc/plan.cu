@@ -58,13 +58,22 @@ __global__ void k_class_flags(TrieView tv, uint32_t n, uint32_t light_max, int c
     flags[u] = f ? 1u : 0u;
 }
 
+// cost on a 14-bit logarithmic scale: the exponent and the next 8 bits
+// (monotone in the cost, 0.3% resolution: enough to put the heaviest first)
+constexpr int COST_BITS = 14;
+
 __global__ void k_class_keys(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
-                             const uint64_t *__restrict__ cost, uint32_t n, int nb, int cbits, uint64_t *keys) {
+                             const uint64_t *__restrict__ cost, uint32_t n, int nb, uint64_t *keys) {
     uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n || !flags[u]) return;
-    uint64_t cmax = (1ull << cbits) - 1;
-    uint64_t c = cost[u] < cmax ? cost[u] : cmax;
-    keys[pos[u]] = ((cmax - c) << nb) | u;   // ascending key = descending cost
+    const uint64_t c = cost[u];
+    uint32_t q = 0;
+    if (c) {
+        const int msb = 63 - __clzll((long long)c);
+        q = (uint32_t)msb * 256u + (uint32_t)(((c << (63 - msb)) >> 55) & 255u);
+    }
+    const uint64_t qmax = (1ull << COST_BITS) - 1;
+    keys[pos[u]] = ((qmax - q) << nb) | u;   // ascending key = descending cost
 }
 
 __global__ void k_key_ids(const uint64_t *__restrict__ keys, uint32_t cnt, int nb, uint32_t *ids) {
@@ -87,10 +96,9 @@ eh_status make_list(TrieView tv, uint32_t n, int nb, uint32_t light_max, int cls
     uint64_t *k1 = nullptr, *k2 = nullptr;
     if (st == EH_OK) st = dev_alloc(&k1, cnt, s);
     if (st == EH_OK) st = dev_alloc(&k2, cnt, s);
-    int cbits = 64 - nb < 40 ? 64 - nb : 40;
     if (st == EH_OK && cnt) {
-        k_class_keys<<<blocks, 256, 0, s>>>(flags, pos, cost, n, nb, cbits, k1);
-        st = dev_radix_sort_u64(&k1, &k2, cnt, nb + cbits, s);
+        k_class_keys<<<blocks, 256, 0, s>>>(flags, pos, cost, n, nb, k1);
+        st = dev_radix_sort_u64(&k1, &k2, cnt, nb + COST_BITS, s);
     }
     uint32_t *ids = nullptr;
     if (st == EH_OK) {

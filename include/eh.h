@@ -219,7 +219,7 @@ eh_status eh_count_status(const eh_trie *trie, void *stream);
  * library keeps until the process exits.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current.
  * The 4-clique pattern needs max out-degree x launch warps x 4 bytes of arena
- * when the max out-degree exceeds 1024; above 32 MiB the call returns
+ * when the max out-degree exceeds 512; above 32 MiB the call returns
  * EH_EINVAL with the sizes in eh_last_error, before launching anything.
  * All calls share the array (each clears its counters first): calls whose
  * work overlaps on the GPU, on any trie or stream, race and must not be

@@ -409,7 +409,7 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     for (uint32_t i = 0; i < nq; ++i) any_k4 |= h_qpat[i] == EH_CLIQUE4;
     uint32_t *arena = nullptr;
     const uint64_t per_warp = ((uint64_t)maxlen + 3) & ~3ull;
-    if (any_k4 && maxlen > 1024) {
+    if (any_k4 && maxlen > K4_S_CAP) {
         uint32_t gw = 0;
         EH_TRY(eh_launch_batch(bv, heavy, n_heavy, light, n_light, xo, s, nullptr, nullptr, nullptr, nullptr, 0, &gw));
         EH_TRY(sc.alloc(&arena, per_warp * gw));

@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
 // warp's slice of a global arena when |S| may exceed it.  Level 2 runs the
 // same layout-dispatched intersection as the triangle on (S_<z, N+(z)).
 
-constexpr uint32_t S_CAP = 512;    // per-warp shared S buffer (elements; 512 measured faster than 1024)
+constexpr uint32_t S_CAP = K4_S_CAP;
 constexpr uint32_t K4_PAIR_BATCH = 1;   // (x, y) pairs are heavy and uneven: one at a time
 constexpr uint32_t SB_CAP_WORDS = 256;    // per-warp bitmap of S: value ranges up to 8,192
 constexpr uint32_t LANE_UINT_MAX = 64;    // a lane walks a uint N+(z) alone up to this length

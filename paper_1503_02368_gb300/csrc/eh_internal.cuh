@@ -207,6 +207,12 @@ eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan *
 // TRI_MODE_APEX: each work item's triangles in which it is the largest id, to
 // d_vt[item] for heavy items and d_vt[n_heavy + i] for light item i
 constexpr int TRI_MODE_APEX = 3;
+
+// per-warp shared buffer of the 4-clique's materialised S = N+(x) ∩ N+(y), in
+// elements, in the count and batch kernels; a set longer than this needs the
+// global spill arena (512 measured faster than 1024: a smaller shared carve-out
+// leaves more L1)
+constexpr uint32_t K4_S_CAP = 512;
 eh_status eh_launch_triangle(const eh_trie *t, const WorkPlan &plan, TrieView tv, int mode,
                              const eh_exec_opts &xo, cudaStream_t s, unsigned long long *d_acc,
                              unsigned long long *d_counters, uint32_t *d_status, unsigned long long *d_vt,

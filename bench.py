@@ -38,7 +38,7 @@ WORKLOAD = "rmat_s22_ef16 triangle: R-MAT scale 22, edge factor 16, (a,b,c,d)=(.
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="eh", choices=["eh", "reference"])
     ap.add_argument("--tau", type=int, default=None,
@@ -87,15 +87,29 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
+        self.skip = 0
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", str(period_ms)], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+
+    def _lines(self):
+        with open(self.f.name) as g:
+            return sum(1 for _ in g)
+
+    def start(self, wait_s=3.0):
+        """Wait for the sampler's first row, then count only rows written after this call."""
+        if self.p is None:
+            return
+        t0 = time.time()
+        while self._lines() == 0 and self.p.poll() is None and time.time() - t0 < wait_s:
+            time.sleep(0.02)
+        self.skip = self._lines()
 
     def stop(self):
         if self.p is None:
@@ -107,9 +121,9 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         rows = []
-        for line in open(self.f.name):
+        for i, line in enumerate(open(self.f.name)):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
+            if i >= self.skip and len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.f.name)
         if not rows:
@@ -527,6 +541,7 @@ def run_eh(args):
         torch.distributed.barrier()
 
     clocks = Clocks(local)
+    clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     if world > 1:

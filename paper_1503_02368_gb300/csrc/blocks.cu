@@ -11,11 +11,11 @@
 //                      the set's uint array, bits 23..30 = run length - 1
 // A trie built with EH_BUILD_BLOCK_LAYOUT holds these directories instead of
 // set-level bitsets.  Its triangle count intersects two sets by their
-// directories: the lanes of a warp walk the shorter directory, find each
-// block id in the longer one by binary search (the offsets-as-uint
-// intersection of Sec. 4.2), and intersect matching blocks by the layout pair:
-// AND + popcount of 8 words, bit probes of a run's values, or a merge of two
-// runs.
+// directories, the block ids treated as a uint set (Sec. 4.2): each id of one
+// directory is found in the other by binary search (in shared memory, where
+// u's directory is staged), and matching blocks are intersected by their
+// layout pair: AND + popcount of 8 words, bit probes of a run's values, or a
+// merge of two runs.
 #include "eh_internal.cuh"
 
 #include <algorithm>
@@ -127,47 +127,223 @@ __device__ __forceinline__ uint32_t block_meet(uint32_t ia, const uint32_t *Sa, 
     return c;
 }
 
-// one warp per vertex u (any order); v runs over N+(u); counts |N+(u) ∩ N+(v)|
-__global__ void k_tri_blocks(TrieView tv, const uint64_t *__restrict__ boff, const uint2 *__restrict__ dir,
-                             const uint32_t *__restrict__ words, const uint32_t *__restrict__ items,
-                             uint32_t n_items, unsigned int *next, unsigned long long *out) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long acc = 0;
-    for (;;) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(next, 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= n_items) break;
-        const uint32_t u = items[it];
-        const SetDesc du = tv.desc[u];
-        const uint32_t *Sa = tv.nbr + du.off;
-        const uint2 *da = dir + boff[u];
-        const uint32_t na = (uint32_t)(boff[u + 1] - boff[u]);
-        for (uint32_t j = 1; j < du.len; ++j) {
-            const uint32_t v = __ldg(&Sa[j]);
-            const SetDesc dv = tv.desc[v];
-            if (dv.len == 0) continue;
-            const uint32_t *Sb = tv.nbr + dv.off;
-            const uint2 *db = dir + boff[v];
-            const uint32_t nbk = (uint32_t)(boff[v + 1] - boff[v]);
-            // walk the shorter directory, search the longer one
-            const bool a_short = na <= nbk;
-            const uint2 *ds = a_short ? da : db, *dl = a_short ? db : da;
-            const uint32_t ns = a_short ? na : nbk, nl = a_short ? nbk : na;
-            const uint32_t *Ss = a_short ? Sa : Sb, *Sl = a_short ? Sb : Sa;
-            for (uint32_t i = lane; i < ns; i += 32) {
-                const uint2 e = ds[i];
-                uint32_t lo = 0, hi = nl;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (dl[mid].x < e.x) lo = mid + 1; else hi = mid;
-                }
-                if (lo < nl && dl[lo].x == e.x) acc += block_meet(e.y, Ss, dl[lo].y, Sl, words);
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr int BLK_WARPS = 8;                       // warps per CTA of the block-layout count
+constexpr uint32_t U_CAP = 512;                    // u's directory entries a warp stages (light u)
+constexpr uint32_t CTA_CAP = BLK_WARPS * U_CAP;    // ... a CTA stages (heavy u), in the same buffer
+constexpr uint32_t BIG_LEN = 256;                   // a longer N+(u) is shared by a CTA
+constexpr uint32_t SKEW = 8;           // a directory longer than SKEW x u's (and than SKEW_MIN) is searched,
+constexpr uint32_t SKEW_MIN = 256;     // not walked
+
+// a warp's batch of 32 v's
+struct BlkBatch {
+    unsigned long long vb[32];       // first directory entry of each v
+    uint32_t pre[32];                // exclusive prefix of the walked directory lengths
+    uint32_t voff[32];               // offset of each v's uint array
+};
+
+// smallest index i in [0, n) with d[i].x >= id, or n
+__device__ __forceinline__ uint32_t dir_lower_bound(const uint2 *d, uint32_t n, uint32_t id) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d[mid].x < id) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Sum of |block ∩ block| over the block ids two directories share: the lanes
+// walk the shorter one and find each id in the longer one by binary search.
+__device__ __forceinline__ unsigned long long meet_searched(const uint2 *da, uint32_t na, const uint32_t *Sa,
+                                                            const uint2 *db, uint32_t nb, const uint32_t *Sb,
+                                                            const uint32_t *__restrict__ words, int lane) {
+    const bool a_short = na <= nb;
+    const uint2 *ds = a_short ? da : db, *dl = a_short ? db : da;
+    const uint32_t ns = a_short ? na : nb, nl = a_short ? nb : na;
+    const uint32_t *Ss = a_short ? Sa : Sb, *Sl = a_short ? Sb : Sa;
+    unsigned long long c = 0;
+    for (uint32_t i = lane; i < ns; i += 32) {
+        const uint2 e = ds[i];
+        const uint32_t k = dir_lower_bound(dl, nl, e.x);
+        if (k < nl) {
+            const uint2 f = dl[k];
+            if (f.x == e.x) c += block_meet(e.y, Ss, f.y, Sl, words);
+        }
+    }
+    return c;
+}
+
+// v = N+(u)[j] for j in [j0, j1) (at most 32), each intersected with u's
+// directory: through ud (u's directory staged in shared memory) when staged,
+// else by meet_searched on global memory.  With ud, the v's directories form
+// one list of entries that the lanes walk in step, each entry's block id found
+// among u's staged ids by binary search; a v whose directory is far longer
+// than u's is searched instead (the lanes walk u's entries).
+__device__ __forceinline__ void blk_pairs(const TrieView &tv, const uint64_t *__restrict__ boff,
+                                          const uint2 *__restrict__ dir, const uint32_t *__restrict__ words,
+                                          const uint32_t *Su, const uint2 *da, const uint2 *ud, uint32_t na,
+                                          uint32_t j0, uint32_t j1, BlkBatch &b, int lane,
+                                          unsigned long long &acc) {
+    const uint32_t j = j0 + lane;
+    uint32_t nb = 0, voff = 0;
+    uint64_t bv = 0;
+    if (j < j1) {
+        const uint32_t v = __ldg(&Su[j]);
+        bv = boff[v];
+        nb = (uint32_t)(boff[v + 1] - bv);
+        voff = tv.desc[v].off;
+    }
+    if (!ud) {
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t nbk = __shfl_sync(FULL, nb, k);
+            const uint64_t bk = __shfl_sync(FULL, bv, k);
+            const uint32_t vk = __shfl_sync(FULL, voff, k);
+            if (nbk) acc += meet_searched(da, na, Su, dir + bk, nbk, tv.nbr + vk, words, lane);
+        }
+        return;
+    }
+    const bool skew = nb > SKEW * na && nb > SKEW_MIN;
+    const uint32_t walk = skew ? 0u : nb;
+    uint32_t incl = walk;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    __syncwarp();                   // the previous batch's readers are done
+    b.pre[lane] = incl - walk;
+    b.voff[lane] = voff;
+    b.vb[lane] = bv;
+    __syncwarp();
+    for (uint32_t e = lane; e < total; e += 32) {
+        // the owner: the largest k with pre[k] <= e (a v with nothing to walk
+        // shares its prefix with the next lane, which then wins)
+        uint32_t lo = 0, hi = 31;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (b.pre[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const uint2 ev = dir[b.vb[lo] + (e - b.pre[lo])];
+        const uint32_t k = dir_lower_bound(ud, na, ev.x);
+        if (k < na) {
+            const uint2 eu = ud[k];
+            if (eu.x == ev.x) acc += block_meet(eu.y, Su, ev.y, tv.nbr + b.voff[lo], words);
+        }
+    }
+    unsigned m = __ballot_sync(FULL, skew);
+    while (m) {
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t nbk = __shfl_sync(FULL, nb, k);
+        const uint2 *dv = dir + b.vb[k];
+        const uint32_t *Sv = tv.nbr + b.voff[k];
+        for (uint32_t i = lane; i < na; i += 32) {
+            const uint2 eu = ud[i];
+            const uint32_t p = dir_lower_bound(dv, nbk, eu.x);
+            if (p < nbk) {
+                const uint2 ev = dv[p];
+                if (ev.x == eu.x) acc += block_meet(eu.y, Su, ev.y, Sv, words);
             }
         }
     }
-    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+}
+
+__device__ __forceinline__ bool is_big(const TrieView &tv, const uint64_t *__restrict__ boff, uint32_t u) {
+    return tv.desc[u].len > BIG_LEN || boff[u + 1] - boff[u] > U_CAP;
+}
+
+// For every work item u, v runs over N+(u) (v = min N+(u) excluded: nothing
+// lies below it in N+(u)) and |N+(u) ∩ N+(v)| is added: the triangles
+// (u, v, w) with w < v < u.
+// The heavy list comes big items first (|N+(u)| > BIG_LEN, or a directory of
+// more than U_CAP entries), heaviest first.  Big items: one CTA each; the CTA
+// stages u's directory (up to CTA_CAP entries) and its warps take v's 32 at a
+// time.  Every other item, of the heavy list and then of the light list: one
+// warp each, u's directory staged in the warp's slice of the same buffer.
+__global__ void __launch_bounds__(BLK_WARPS * 32, 6) k_tri_blocks(TrieView tv, const uint64_t *__restrict__ boff,
+                                                                  const uint2 *__restrict__ dir,
+                                                                  const uint32_t *__restrict__ words,
+                                                                  const uint32_t *__restrict__ heavy,
+                                                                  uint32_t n_big, uint32_t n_heavy,
+                                                                  const uint32_t *__restrict__ light,
+                                                                  uint32_t n_light, unsigned int *next,
+                                                                  unsigned long long *out) {
+    constexpr uint32_t NT = BLK_WARPS * 32;
+    __shared__ uint2 s_dir[CTA_CAP];
+    __shared__ BlkBatch s_bat[BLK_WARPS];
+    __shared__ uint32_t s_item, s_next;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    BlkBatch &b = s_bat[warp];
+    unsigned long long acc = 0;
+
+    for (;;) {   // big items: one CTA each
+        if (tid == 0) {
+            s_item = atomicAdd(&next[0], 1u);
+            s_next = 1;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_big) break;
+        const uint32_t u = heavy[item];
+        const SetDesc du = tv.desc[u];
+        const uint32_t *Su = tv.nbr + du.off;
+        const uint64_t bu = boff[u];
+        const uint32_t na = (uint32_t)(boff[u + 1] - bu);
+        const uint2 *da = dir + bu;
+        const bool staged = na <= CTA_CAP;
+        if (staged)
+            for (uint32_t e = tid; e < na; e += NT) s_dir[e] = da[e];
+        __syncthreads();
+        for (;;) {
+            uint32_t j0 = 0;
+            if (lane == 0) j0 = atomicAdd(&s_next, 32u);
+            j0 = __shfl_sync(FULL, j0, 0);
+            if (j0 >= du.len) break;
+            blk_pairs(tv, boff, dir, words, Su, da, staged ? s_dir : nullptr, na, j0, min(j0 + 32, du.len), b,
+                      lane, acc);
+        }
+        __syncthreads();   // the staged directory, s_item and s_next are done with before the next u
+    }
+
+    uint2 *ud = s_dir + warp * U_CAP;
+    const uint32_t n_rest = n_heavy - n_big;
+    for (;;) {   // every other item: one warp each, the rest of the heavy list and then the light list
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&next[1], 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= n_rest + n_light) break;
+        const uint32_t u = it < n_rest ? heavy[n_big + it] : light[it - n_rest];
+        const SetDesc du = tv.desc[u];
+        if (du.len < 2) continue;
+        const uint32_t *Su = tv.nbr + du.off;
+        const uint64_t bu = boff[u];
+        const uint32_t na = (uint32_t)(boff[u + 1] - bu);
+        const uint2 *da = dir + bu;
+        const bool staged = na <= U_CAP;
+        __syncwarp();                       // the previous u's readers are done
+        if (staged)
+            for (uint32_t e = lane; e < na; e += 32) ud[e] = da[e];
+        __syncwarp();
+        for (uint32_t j0 = 1; j0 < du.len; j0 += 32)
+            blk_pairs(tv, boff, dir, words, Su, da, staged ? ud : nullptr, na, j0, min(j0 + 32, du.len), b, lane,
+                      acc);
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
     if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
+// 1 for a big heavy item (a CTA's work in k_tri_blocks), else 0
+__global__ void k_big_flags(TrieView tv, const uint64_t *__restrict__ boff, const uint32_t *__restrict__ heavy,
+                            uint32_t n, uint32_t *flags) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = is_big(tv, boff, heavy[i]) ? 1u : 0u;
+}
+
+// stable partition: big items first, each part in list order
+__global__ void k_big_scatter(const uint32_t *__restrict__ heavy, const uint32_t *__restrict__ flags,
+                              const uint32_t *__restrict__ pos, uint32_t n, uint32_t n_big, uint32_t *out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[flags[i] ? pos[i] : n_big + (i - pos[i])] = heavy[i];
 }
 
 }  // namespace
@@ -212,19 +388,53 @@ eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s) {
     return EH_OK;
 }
 
+eh_status eh_plan_blocks(eh_trie *t, WorkPlan *p, cudaStream_t s) {
+    const uint32_t n = p->n_heavy;
+    uint32_t *flags = nullptr, *pos = nullptr;
+    EH_TRY(dev_alloc(&flags, n, s));
+    eh_status st = dev_alloc(&pos, n, s);
+    uint64_t n_big = 0;
+    if (st == EH_OK) {   // held by the plan, freed with its other lists
+        cudaError_t e = eh_alloc_should_fail() ? cudaErrorMemoryAllocation
+                                               : cudaMalloc((void **)&p->d_heavy_blk, (n ? n : 1) * 4ull);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->d_heavy_blk = nullptr;
+            eh_set_error("block plan: allocation failed");
+            st = EH_ENOMEM;
+        }
+    }
+    if (st == EH_OK && n) {
+        k_big_flags<<<blocks_for(n), 256, 0, s>>>(t->view(), t->d_boff, p->d_heavy, n, flags);
+        st = dev_exclusive_scan_u32(flags, pos, n, s, &n_big);
+    }
+    if (st == EH_OK && n) {
+        k_big_scatter<<<blocks_for(n), 256, 0, s>>>(p->d_heavy, flags, pos, n, (uint32_t)n_big, p->d_heavy_blk);
+        if (cudaGetLastError() != cudaSuccess) { eh_set_error("block plan: launch failed"); st = EH_ECUDA; }
+    }
+    dev_free(flags, s);
+    dev_free(pos, s);
+    if (st != EH_OK) {
+        cudaFree(p->d_heavy_blk);
+        p->d_heavy_blk = nullptr;
+        return st;
+    }
+    p->n_big = (uint32_t)n_big;
+    return EH_OK;
+}
+
 eh_status eh_launch_tri_blocks(eh_trie *t, const WorkPlan &plan, cudaStream_t s, unsigned long long *d_acc,
                                unsigned int *d_next) {
-    const uint32_t n_items = plan.n_heavy + plan.n_light;
-    if (!n_items) return EH_OK;
-    // heavy items, then light ones (the plan's two lists), a counter each
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)eh_num_sms() * 8, (n_items + 7) / 8);
+    if (!plan.n_heavy && !plan.n_light) return EH_OK;
+    if (plan.n_heavy && !plan.d_heavy_blk) { eh_set_error("block layout: the work plan has no block order"); return EH_EINVAL; }
+    int per_sm = 0;
+    EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_blocks, BLK_WARPS * 32, 0));
+    const uint64_t want = plan.n_big + ((uint64_t)(plan.n_heavy - plan.n_big) + plan.n_light + BLK_WARPS - 1) / BLK_WARPS;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>((uint64_t)eh_num_sms() * (uint32_t)std::max(1, per_sm), want));
     EH_CUDA_TRY(cudaMemsetAsync(d_next, 0, 8, s));
-    if (plan.n_heavy)
-        k_tri_blocks<<<std::max(1u, std::min(grid, (plan.n_heavy + 7) / 8)), 256, 0, s>>>(
-            t->view(), t->d_boff, t->d_bdir, t->d_bwords, plan.d_heavy, plan.n_heavy, d_next, d_acc);
-    if (plan.n_light)
-        k_tri_blocks<<<std::max(1u, std::min(grid, (plan.n_light + 7) / 8)), 256, 0, s>>>(
-            t->view(), t->d_boff, t->d_bdir, t->d_bwords, plan.d_light, plan.n_light, d_next + 1, d_acc);
+    k_tri_blocks<<<grid, BLK_WARPS * 32, 0, s>>>(t->view(), t->d_boff, t->d_bdir, t->d_bwords, plan.d_heavy_blk,
+                                                 plan.n_big, plan.n_heavy, plan.d_light, plan.n_light, d_next, d_acc);
     EH_CUDA_TRY(cudaGetLastError());
     return EH_OK;
 }

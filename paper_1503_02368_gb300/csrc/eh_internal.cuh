@@ -94,6 +94,8 @@ struct WorkPlan {
     uint32_t n_heavy = 0;
     uint32_t *d_light = nullptr;   // 2 <= |N+(u)| <= light_max
     uint32_t n_light = 0;
+    uint32_t *d_heavy_blk = nullptr;   // block layout only: the heavy list, big items first (blocks.cu)
+    uint32_t n_big = 0;
     double alg_bytes = 0;          // algorithmic bytes of one triangle pass
     double alg_bytes_k4 = 0;       // algorithmic bytes of one 4-clique pass
 };
@@ -237,6 +239,8 @@ eh_status eh_vertex_order(uint32_t ordering, uint32_t seed, const uint64_t *ukey
 // composite layout: build the directories of the pruned sets; the triangle
 // count over them (adds into d_acc; d_next = 2 zeroed counters) (blocks.cu)
 eh_status eh_build_blocks(eh_trie *t, uint32_t tau, cudaStream_t s);
+// the block-layout count's order of the heavy list (plan.d_heavy_blk, n_big)
+eh_status eh_plan_blocks(eh_trie *t, WorkPlan *p, cudaStream_t s);
 eh_status eh_launch_tri_blocks(eh_trie *t, const WorkPlan &plan, cudaStream_t s, unsigned long long *d_acc,
                                unsigned int *d_next);
 // fills eh_trie::h_out_by_old if not yet built (trie_build.cu)

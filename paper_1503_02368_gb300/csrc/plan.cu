@@ -137,6 +137,7 @@ eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan *
         st = make_list(tv, t->n, t->nb, light_max, 0, cost, s, &p.d_heavy, &p.n_heavy);
     }
     if (st == EH_OK) st = make_list(tv, t->n, t->nb, light_max, 1, cost, s, &p.d_light, &p.n_light);
+    if (st == EH_OK && t->d_boff) st = eh_plan_blocks(t, &p, s);
     unsigned long long bytes_h = 0;
     if (st == EH_OK) {
         cudaMemcpyAsync(&bytes_h, bytes_d, 8, cudaMemcpyDeviceToHost, s);
@@ -147,6 +148,7 @@ eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan *
     if (st != EH_OK) {
         cudaFree(p.d_heavy);
         cudaFree(p.d_light);
+        cudaFree(p.d_heavy_blk);
         return st;
     }
     p.alg_bytes = (double)bytes_h + 8.0 * (double)t->m;

@@ -236,7 +236,11 @@ void free_trie_arrays(eh_trie *t) {
     for (void *p : pooled)
         if (p) cudaFreeAsync(p, 0);
     cudaFree(t->d_arena);
-    for (auto &kv : t->plans) { cudaFree(kv.second.d_heavy); cudaFree(kv.second.d_light); }
+    for (auto &kv : t->plans) {
+        cudaFree(kv.second.d_heavy);
+        cudaFree(kv.second.d_light);
+        cudaFree(kv.second.d_heavy_blk);
+    }
     t->plans.clear();
 }
 

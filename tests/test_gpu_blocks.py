@@ -80,6 +80,29 @@ def test_block_layout_under_other_orderings(eh, ordering):
     assert t.count("triangle") == want
 
 
+@pytest.mark.parametrize("ordering", ("random", "degree"))
+def test_block_layout_long_directories(eh, ordering):
+    # Chung-Lu hubs over 1,024 block ids.  Under a random order some pruned sets
+    # touch more than 512 blocks (more than a warp stages in shared memory), and
+    # light u's meet hub v's whose directories are over 8x longer than theirs
+    # and over 256 entries (searched rather than walked).
+    import synth
+    n = 1 << 18
+    s, d = synth.chunglu(n, 1_500_000, synth.key(1503, 95), gamma=2.1)
+    want = oracle.Graph(n, s, d).triangles()
+    for tau in (1, 256):
+        t = eh.Trie(s, d, n, tau=tau, ordering=ordering, order_seed=3, block_layout=True)
+        assert t.count("triangle") == want, tau
+    x = t.export(0)
+    off, _, _ = t.export_blocks()
+    na = np.diff(off.astype(np.int64))
+    u = np.repeat(np.arange(n), x["len"].astype(np.int64))
+    v = np.concatenate([x["nbr"][int(b):int(b) + int(ln)] for b, ln in zip(x["off"], x["len"])]).astype(np.int64)
+    skew = int(((na[v] > 8 * na[u]) & (na[v] > 256)).sum())
+    if ordering == "random":
+        assert na.max() > 512 and skew > 0, (na.max(), skew)
+
+
 def test_export_blocks_needs_the_layout(eh):
     s, d = G.arrays(G.complete(5))
     t = eh.Trie(s, d, 5, tau=32)

@@ -155,8 +155,9 @@ eh_status dev_exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, 
                                  uint64_t *total_host);
 eh_status dev_exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
                                  uint64_t *total_host);
-// Stable LSD radix sort of keys on bits [0, key_bits); result in *keys
-// (the two buffers may be swapped on return).
+// Stable LSD radix sort of keys on bits [0, key_bits) (bits above are ignored,
+// not required to be zero); result in *keys (the two buffers may be swapped
+// on return).
 eh_status dev_radix_sort_u64(uint64_t **keys, uint64_t **tmp, uint64_t n, int key_bits, cudaStream_t s);
 
 // Allocation-failure injection for tests (eh_test_fail_alloc_after): when

@@ -101,25 +101,25 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_BINS = 256;
 
 __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint64_t *__restrict__ keys, uint64_t n, uint64_t chunk,
-                                                           int shift, uint32_t *hist) {
+                                                           int shift, uint32_t dmask, uint32_t *hist) {
     __shared__ uint32_t h[RS_BINS];
     const int tid = threadIdx.x;
     for (int b = tid; b < RS_BINS; b += RS_THREADS) h[b] = 0;
     __syncthreads();
     uint64_t begin = (uint64_t)blockIdx.x * chunk;
     uint64_t end = begin + chunk < n ? begin + chunk : n;
-    for (uint64_t i = begin + tid; i < end; i += RS_THREADS) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    for (uint64_t i = begin + tid; i < end; i += RS_THREADS) atomicAdd(&h[(keys[i] >> shift) & dmask], 1u);
     __syncthreads();
     for (int b = tid; b < RS_BINS; b += RS_THREADS) hist[(uint64_t)b * gridDim.x + blockIdx.x] = h[b];
 }
 
-// Stable scatter of one 8-bit digit.  Per tile: every warp ranks its keys
-// among the keys of the same digit (match_any, in input order), the tile's
+// Stable scatter of one digit of up to 8 bits (dmask).  Per tile: every warp
+// ranks its keys among the keys of the same digit (match_any, in input order), the tile's
 // keys are placed in digit order in shared memory, and each digit's run is
 // then written to its global range with consecutive threads on consecutive
 // addresses (coalesced), instead of one scattered store per key.
 __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
-                                                             uint64_t n, uint64_t chunk, int shift,
+                                                             uint64_t n, uint64_t chunk, int shift, uint32_t dmask,
                                                              const uint32_t *__restrict__ offs) {
     __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];   // per-warp digit counts, then the warps' offsets in the digit's run
     __shared__ uint32_t run[RS_BINS];              // global position of the digit's next key
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint64_t *__res
             const uint64_t idx = sub + (uint64_t)r * 32 + lane;
             const bool valid = idx < end;
             k[r] = valid ? in[idx] : 0ull;
-            dig[r] = valid ? (uint32_t)(k[r] >> shift) & 255u : 256u;   // 256: no key
+            dig[r] = valid ? (uint32_t)(k[r] >> shift) & dmask : 256u;   // 256: no key
             const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
             const uint32_t before = valid ? wcnt[warp][dig[r]] : 0u;     // this warp's earlier keys of the digit
             __syncwarp();
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint64_t *__res
         const uint32_t cnt = (uint32_t)(end - tile < (uint64_t)RS_TILE ? end - tile : (uint64_t)RS_TILE);
         for (uint32_t i = tid; i < cnt; i += RS_THREADS) {
             const uint64_t key = skey[i];
-            const uint32_t d = (uint32_t)(key >> shift) & 255u;
+            const uint32_t d = (uint32_t)(key >> shift) & dmask;
             out[run[d] + (i - loc[d])] = key;
         }
         __syncthreads();
@@ -220,10 +220,13 @@ eh_status dev_radix_sort_u64(uint64_t **keys, uint64_t **tmp, uint64_t n, int ke
     EH_TRY(dev_alloc(&hist, RS_BINS * G, s));
     eh_status st = EH_OK;
     for (int shift = 0; shift < key_bits; shift += 8) {
-        rs_upsweep<<<(unsigned)G, RS_THREADS, 0, s>>>(*keys, n, chunk, shift, hist);
+        // the last digit keeps only the bits below key_bits: bits above them
+        // need not be zero (a sort on the low field of a packed key)
+        const uint32_t dmask = key_bits - shift >= 8 ? 255u : (1u << (key_bits - shift)) - 1u;
+        rs_upsweep<<<(unsigned)G, RS_THREADS, 0, s>>>(*keys, n, chunk, shift, dmask, hist);
         st = dev_exclusive_scan_u32(hist, hist, RS_BINS * G, s, nullptr);
         if (st != EH_OK) break;
-        rs_downsweep<<<(unsigned)G, RS_THREADS, 0, s>>>(*keys, *tmp, n, chunk, shift, hist);
+        rs_downsweep<<<(unsigned)G, RS_THREADS, 0, s>>>(*keys, *tmp, n, chunk, shift, dmask, hist);
         uint64_t *t = *keys;
         *keys = *tmp;
         *tmp = t;

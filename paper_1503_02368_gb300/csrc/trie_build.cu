@@ -120,14 +120,25 @@ __global__ void k_stats(const uint32_t *__restrict__ deg, const uint32_t *__rest
     }
 }
 
-__global__ void k_directed_keys(const uint64_t *__restrict__ ukeys, uint64_t m, int nb,
-                                const uint32_t *__restrict__ old2new, uint64_t *dk) {
+// each unique edge once as (hi, lo) in new ids, hi > lo
+__global__ void k_pruned_keys(const uint64_t *__restrict__ ukeys, uint64_t m, int nb,
+                              const uint32_t *__restrict__ old2new, uint64_t *dk) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     uint64_t k = ukeys[i];
     uint32_t a = old2new[(uint32_t)(k >> nb)], b = old2new[(uint32_t)(k & ((1ull << nb) - 1))];
-    dk[2 * i] = ((uint64_t)a << nb) | b;
-    dk[2 * i + 1] = ((uint64_t)b << nb) | a;
+    uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+    dk[i] = ((uint64_t)hi << nb) | lo;
+}
+
+// |N+(v)|: the run length of each high endpoint in keys sorted by it (lanes of
+// the same run add once per warp)
+__global__ void k_count_hi(const uint64_t *__restrict__ keys, uint64_t m, int nb, uint32_t *cnt) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < m;
+    const uint32_t v = valid ? (uint32_t)(keys[i] >> nb) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, v);
+    if (valid && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0) atomicAdd(&cnt[v], (uint32_t)__popc(peers));
 }
 
 __global__ void k_round4(const uint32_t *__restrict__ x, uint64_t n, uint64_t *out) {
@@ -140,38 +151,40 @@ __global__ void k_widen(const uint32_t *__restrict__ x, uint64_t n, uint64_t *ou
     if (i < n) out[i] = x[i];
 }
 
-// place sorted directed edge i = (v, w) at soff[v] + (i - ustart[v])
-__global__ void k_fill_sym(const uint64_t *__restrict__ dk, uint64_t n2, int nb, const uint64_t *__restrict__ ustart,
-                           const uint64_t *__restrict__ soff, uint32_t *snbr) {
+__global__ void k_widen_diff(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, uint64_t n,
+                             uint64_t *out) {
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n2) return;
-    uint64_t k = dk[i];
-    uint32_t v = (uint32_t)(k >> nb), w = (uint32_t)(k & ((1ull << nb) - 1));
-    snbr[soff[v] + (i - ustart[v])] = w;
+    if (i < n) out[i] = (uint64_t)(a[i] - b[i]);
 }
 
-// |N+(v)| = the number of entries of the sorted N(v) below v (binary search)
-__global__ void k_out_degree(const uint32_t *__restrict__ snbr, const uint64_t *__restrict__ soff,
-                             const uint32_t *__restrict__ deg, uint32_t n, uint32_t *odeg) {
-    const uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const uint32_t *N = snbr + soff[v];
-    uint32_t lo = 0, hi = deg[v];
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (N[mid] < (uint32_t)v) lo = mid + 1; else hi = mid;
-    }
-    odeg[v] = lo;
+// keys sorted by (v, w), w < v: entry i is element i - astart[v] of N+(v),
+// which is also the lower part of N(v)
+// (an entry outside its vertex's range, which sorted input rules out, is not
+// written and sets the status word)
+__global__ void k_fill_lower(const uint64_t *__restrict__ A, uint64_t m, int nb, uint32_t n,
+                             const uint64_t *__restrict__ astart, const uint64_t *__restrict__ soff,
+                             const uint64_t *__restrict__ ooff, uint32_t *snbr, uint32_t *onbr, uint32_t *status) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint64_t k = A[i];
+    const uint32_t v = (uint32_t)(k >> nb), w = (uint32_t)(k & ((1ull << nb) - 1));
+    if (v >= n || i < astart[v] || i >= astart[v + 1]) { atomicOr(status, DEV_ST_RANGE); return; }
+    const uint64_t j = i - astart[v];
+    snbr[soff[v] + j] = w;
+    onbr[ooff[v] + j] = w;
 }
 
-// N+(v) is the prefix of N(v) below v
-__global__ void k_fill_pruned(const uint32_t *__restrict__ snbr, const uint64_t *__restrict__ soff,
-                              const uint64_t *__restrict__ ooff, const uint32_t *__restrict__ odeg, uint32_t n,
-                              uint32_t *onbr) {
-    uint32_t v = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (v >= n) return;
-    uint32_t len = odeg[v];
-    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) onbr[ooff[v] + j] = snbr[soff[v] + j];
+// the same keys re-sorted stably by w alone: for each w, its larger neighbours
+// v in ascending order, the upper part of N(w) after its |N+(w)| lower entries
+__global__ void k_fill_upper(const uint64_t *__restrict__ B, uint64_t m, int nb, uint32_t n,
+                             const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ soff,
+                             const uint32_t *__restrict__ odeg, uint32_t *snbr, uint32_t *status) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint64_t k = B[i];
+    const uint32_t v = (uint32_t)(k >> nb), w = (uint32_t)(k & ((1ull << nb) - 1));
+    if (w >= n || i < bstart[w] || i >= bstart[w + 1]) { atomicOr(status, DEV_ST_RANGE); return; }
+    snbr[soff[w] + odeg[w] + (i - bstart[w])] = v;
 }
 
 // set-level layout rule (Sec. 4.4): words needed by each set's bitset, 0 = uint
@@ -376,46 +389,63 @@ eh_status build(const uint32_t *src, const uint32_t *dst, uint64_t ne, uint32_t 
     EH_TRY(eh_vertex_order(o.ordering, o.order_seed, ukeys, m, n, nb, deg_old, maxdeg, s, t->d_new2old));
     if (n) k_maps_from_order<<<blocks_for(n), 256, 0, s>>>(t->d_new2old, n, deg_old, t->d_old2new, t->d_deg);
 
-    // 4. both index orders in new ids; symmetric and pruned tries
-    const uint64_t n2 = 2 * m;
+    // 4. the pruned and symmetric tries.  Each edge once as (hi, lo) in new
+    // ids, sorted: N+(v) is v's run.  The same keys re-sorted stably by lo
+    // alone list each vertex's larger neighbours in ascending order, so N(v)
+    // is N+(v) followed by v's run there (every lower neighbour precedes v,
+    // every higher one follows it).
     uint64_t *dk = nullptr, *dk2 = nullptr;
-    EH_TRY(tmp.alloc(&dk, n2));
-    EH_TRY(tmp.alloc(&dk2, n2));
-    if (m) k_directed_keys<<<blocks_for(m), 256, 0, s>>>(ukeys, m, nb, t->d_old2new, dk);
+    EH_TRY(tmp.alloc(&dk, m));
+    EH_TRY(tmp.alloc(&dk2, m));
+    if (m) k_pruned_keys<<<blocks_for(m), 256, 0, s>>>(ukeys, m, nb, t->d_old2new, dk);
     tmp.release(ukeys);
-    EH_TRY(dev_radix_sort_u64(&dk, &dk2, n2, 2 * nb, s));
-    tmp.release(dk2);
+    EH_TRY(dev_radix_sort_u64(&dk, &dk2, m, 2 * nb, s));
+    uint32_t *odeg = nullptr;
+    EH_TRY(tmp.alloc(&odeg, n));
+    EH_CUDA_TRY(cudaMemsetAsync(odeg, 0, (uint64_t)n * 4, s));
+    if (m) k_count_hi<<<blocks_for(m), 256, 0, s>>>(dk, m, nb, odeg);
 
-    uint64_t *ustart = nullptr, *wide = nullptr;
-    EH_TRY(tmp.alloc(&ustart, (uint64_t)n + 1));
+    uint64_t *astart = nullptr, *bstart = nullptr, *wide = nullptr, *ooff = nullptr;
+    EH_TRY(tmp.alloc(&astart, (uint64_t)n + 1));
+    EH_TRY(tmp.alloc(&bstart, (uint64_t)n + 1));
     EH_TRY(tmp.alloc(&wide, (uint64_t)n + 1));
+    EH_TRY(tmp.alloc(&ooff, (uint64_t)n + 1));
+    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
+    if (n) k_widen<<<blocks_for(n), 256, 0, s>>>(odeg, n, wide);
+    EH_TRY(dev_exclusive_scan_u64(wide, astart, (uint64_t)n + 1, s, nullptr));
+    if (n) k_widen_diff<<<blocks_for(n), 256, 0, s>>>(t->d_deg, odeg, n, wide);
+    EH_TRY(dev_exclusive_scan_u64(wide, bstart, (uint64_t)n + 1, s, nullptr));
     EH_TRY(persist_alloc(&t->d_soff, (uint64_t)n + 1, &bytes, s));
-    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
-    if (n) k_widen<<<blocks_for(n), 256, 0, s>>>(t->d_deg, n, wide);
-    EH_TRY(dev_exclusive_scan_u64(wide, ustart, (uint64_t)n + 1, s, nullptr));
-    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
     if (n) k_round4<<<blocks_for(n), 256, 0, s>>>(t->d_deg, n, wide);
     uint64_t slen = 0;
     EH_TRY(dev_exclusive_scan_u64(wide, t->d_soff, (uint64_t)n + 1, s, &slen));
     t->snbr_len = slen;
-    EH_TRY(persist_alloc(&t->d_snbr, slen, &bytes, s));
-    EH_CUDA_TRY(cudaMemsetAsync(t->d_snbr, 0xFF, (slen ? slen : 1) * 4, s));
-    uint32_t *odeg = nullptr;
-    EH_TRY(tmp.alloc(&odeg, n));
-    if (n2) k_fill_sym<<<blocks_for(n2), 256, 0, s>>>(dk, n2, nb, ustart, t->d_soff, t->d_snbr);
-    if (n) k_out_degree<<<blocks_for(n), 256, 0, s>>>(t->d_snbr, t->d_soff, t->d_deg, n, odeg);
-    tmp.release(dk);
-
-    uint64_t *ooff = nullptr;
-    EH_TRY(tmp.alloc(&ooff, (uint64_t)n + 1));
-    EH_CUDA_TRY(cudaMemsetAsync(wide, 0, ((uint64_t)n + 1) * 8, s));
     if (n) k_round4<<<blocks_for(n), 256, 0, s>>>(odeg, n, wide);
     uint64_t olen = 0;
     EH_TRY(dev_exclusive_scan_u64(wide, ooff, (uint64_t)n + 1, s, &olen));
     t->onbr_len = olen;
+    EH_TRY(persist_alloc(&t->d_snbr, slen, &bytes, s));
     EH_TRY(persist_alloc(&t->d_onbr, olen, &bytes, s));
+    EH_CUDA_TRY(cudaMemsetAsync(t->d_snbr, 0xFF, (slen ? slen : 1) * 4, s));
     EH_CUDA_TRY(cudaMemsetAsync(t->d_onbr, 0xFF, (olen ? olen : 1) * 4, s));
-    if (n) k_fill_pruned<<<blocks_for(n, 8), 256, 0, s>>>(t->d_snbr, t->d_soff, ooff, odeg, n, t->d_onbr);
+    if (m)
+        k_fill_lower<<<blocks_for(m), 256, 0, s>>>(dk, m, nb, n, astart, t->d_soff, ooff, t->d_snbr, t->d_onbr,
+                                                   t->d_status);
+    EH_TRY(dev_radix_sort_u64(&dk, &dk2, m, nb, s));
+    if (m) k_fill_upper<<<blocks_for(m), 256, 0, s>>>(dk, m, nb, n, bstart, t->d_soff, odeg, t->d_snbr, t->d_status);
+    {
+        uint32_t st_h = 0;
+        EH_CUDA_TRY(cudaMemcpyAsync(&st_h, t->d_status, 4, cudaMemcpyDeviceToHost, s));
+        EH_CUDA_TRY(cudaStreamSynchronize(s));
+        if (st_h & DEV_ST_RANGE) {
+            eh_set_error("trie build: an adjacency entry fell outside its vertex's range");
+            return EH_ECUDA;
+        }
+    }
+    tmp.release(dk);
+    tmp.release(dk2);
+    tmp.release(astart);
+    tmp.release(bstart);
 
     // 5. layouts
     uint64_t *nwords = nullptr, *woff = nullptr;

@@ -71,6 +71,29 @@ def test_trie_build_matches_oracle(eh, seed):
             assert np.array_equal(np.nonzero(bits)[0] + lo, P)
 
 
+@pytest.mark.parametrize("scale", (13, 17))
+def test_trie_build_id_spaces_off_byte_boundaries(eh, scale):
+    # 13- and 17-bit ids: the build's re-sort on the low endpoint alone must not
+    # mix in the bits of the high endpoint packed above it
+    g = W.rmat_graph(scale, 1503 + scale, edge_factor=8)
+    n = g["n"]
+    o = oracle.Graph(n, g["src"], g["dst"])
+    t = eh.Trie(g["src"], g["dst"], n, tau=32)
+    x, sym = t.export(0), t.export(1)
+    new2old = x["new_to_old"]
+    old2new = np.empty(n, np.int64)
+    old2new[new2old] = np.arange(n)
+    rng = np.random.default_rng(scale)
+    for v in sorted(set(range(64)) | set(rng.choice(n, 1500, replace=False).tolist())):
+        N = np.sort(old2new[o.neighbours(int(new2old[v]))]).astype(np.uint32)
+        b, ln = int(sym["off"][v]), int(sym["len"][v])
+        assert np.array_equal(sym["nbr"][b:b + ln], N), v
+        b, ln = int(x["off"][v]), int(x["len"][v])
+        assert np.array_equal(x["nbr"][b:b + ln], N[N < v]), v
+    for p in ("lollipop", "barbell"):
+        assert t.count(p) == o.count(p, nthreads=8), p
+
+
 def test_invalid_ids_rejected(eh):
     with pytest.raises(eh.EHError) as ei:
         eh.Trie(np.array([0, 5], np.uint32), np.array([1, 2], np.uint32), 5)

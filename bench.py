@@ -159,27 +159,59 @@ def aggregate(edges_per_rank, ms_per_rank_max, world):
     return world * edges_per_rank / (ms_per_rank_max / 1e3)
 
 
+def cpu_model():
+    """The host CPU's model string (x86 'model name', Arm implementer/part), else the machine."""
+    import platform
+    try:
+        names, parts = set(), set()
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k == "model name":
+                names.add(v)
+            elif k in ("CPU implementer", "CPU part"):
+                parts.add("%s %s" % (k, v))
+        if names:
+            return "; ".join(sorted(names))
+        if parts:
+            return "%s (%s)" % (platform.machine(), ", ".join(sorted(parts)))
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(g, seconds, seed=7):
-    """The oracle, as it stands, on a bounded sample of the outer loop."""
+    """The oracle, as it stands, on a bounded sample of the outer loop: on all
+    host cores (the reported value), and single-threaded on a smaller sample."""
     import numpy as np
     import oracle
     cores = os.cpu_count() or 1
     G = oracle.Graph(g["n"], g["src"], g["dst"])
     rng = np.random.default_rng(seed)
     verts = rng.permutation(g["n"]).astype(np.uint32)
-    # grow the sample until it has run `seconds`
-    done_edges, t_total, pos, chunk = 0, 0.0, 0, 4096
-    while t_total < seconds and pos < len(verts):
-        part = verts[pos:pos + chunk]
-        t0 = time.perf_counter()
-        _, e = G.triangles_outer(part, nthreads=cores)
-        t_total += time.perf_counter() - t0
-        done_edges += e
-        pos += len(part)
-        chunk = min(chunk * 2, 1 << 20)
-    return {"value": done_edges / t_total, "unit": "edges/s", "cores": cores, "kind": "oracle",
+
+    def run(nthreads, budget, start):
+        # grow the sample until it has run `budget` seconds
+        done_edges, t_total, pos, chunk = 0, 0.0, start, 4096
+        while t_total < budget and pos < len(verts):
+            part = verts[pos:pos + chunk]
+            t0 = time.perf_counter()
+            _, e = G.triangles_outer(part, nthreads=nthreads)
+            t_total += time.perf_counter() - t0
+            done_edges += e
+            pos += len(part)
+            chunk = min(chunk * 2, 1 << 20)
+        return done_edges, t_total, pos - start
+
+    e_all, t_all, v_all = run(cores, seconds, 0)
+    e_one, t_one, v_one = run(1, seconds / 3, 0)
+    return {"value": e_all / t_all, "unit": "edges/s", "cores": cores, "kind": "oracle",
             "sample": "outer-loop vertices %d of %d (random order, seed %d), %d pruned edges, %.1f s; "
-                      "oracle adjacency build excluded" % (pos, g["n"], seed, done_edges, t_total)}
+                      "oracle adjacency build excluded" % (v_all, g["n"], seed, e_all, t_all),
+            "cpu": cpu_model(),
+            "single_thread": {"value": e_one / t_one, "unit": "edges/s", "cores": 1,
+                              "sample": "the first %d vertices of the same order, %d pruned edges, %.1f s"
+                                        % (v_one, e_one, t_one)}}
 
 
 def bench_batch(eh, tau=32, reps=3, log=None):

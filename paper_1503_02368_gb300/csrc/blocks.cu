@@ -129,11 +129,11 @@ __device__ __forceinline__ uint32_t block_meet(uint32_t ia, const uint32_t *Sa, 
 
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int BLK_WARPS = 8;                       // warps per CTA of the block-layout count
-constexpr uint32_t U_CAP = 512;                    // u's directory entries a warp stages (light u)
-constexpr uint32_t CTA_CAP = BLK_WARPS * U_CAP;    // ... a CTA stages (heavy u), in the same buffer
-constexpr uint32_t BIG_LEN = 256;                   // a longer N+(u) is shared by a CTA
-constexpr uint32_t SKEW = 8;           // a directory longer than SKEW x u's (and than SKEW_MIN) is searched,
-constexpr uint32_t SKEW_MIN = 256;     // not walked
+constexpr uint32_t U_CAP = 512;                    // directory entries of u a warp stages
+constexpr uint32_t CTA_CAP = BLK_WARPS * U_CAP;    // ... a CTA stages for a big item (same buffer)
+constexpr uint32_t BIG_LEN = 256;                  // an item with a longer N+(u) is big: one CTA
+constexpr uint32_t SKEW = 8;                       // a v directory longer than SKEW x u's and than
+constexpr uint32_t SKEW_MIN = 256;                 // SKEW_MIN entries is searched, not walked
 
 // a warp's batch of 32 v's
 struct BlkBatch {

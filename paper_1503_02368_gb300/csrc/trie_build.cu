@@ -5,9 +5,10 @@
 //   2. radix sort + unique: the simple edge relation (m edges);
 //   3. degrees, then new ids by the chosen node ordering (order.cu; default
 //      (degree desc, original id asc), the "Degree" ordering);
-//   4. both index orders of every edge in new ids, radix sorted: the
-//      symmetric trie N(v); its prefix of smaller ids is the pruned trie N+(v)
-//      (each undirected edge kept in the set of its larger endpoint);
+//   4. every edge once as (hi, lo) in new ids, radix sorted: hi's run is the
+//      pruned set N+(hi) (each undirected edge kept in the set of its larger
+//      endpoint) and the lower part of the symmetric set N(hi); the same keys
+//      re-sorted stably on lo alone give the upper part of N(lo);
 //   5. per-set layout: a bitset copy of N+(v) when range <= tau*|N+(v)|.
 #include "eh_internal.cuh"
 

@@ -227,8 +227,10 @@ extern "C" eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, 
     eh_exec_opts xo = eh_exec_defaults(xopts);
     WorkPlan *plan = nullptr;
     EH_TRY(eh_plan_get(t, xo.light_max, (cudaStream_t)stream, &plan));
+    double alg = 0;
+    if (pattern != EH_CLIQUE4) EH_TRY(eh_plan_alg_bytes(t, plan, (cudaStream_t)stream, &alg));
     memset(out, 0, sizeof(*out));
-    out->alg_bytes = pattern == EH_CLIQUE4 ? plan->alg_bytes_k4 : plan->alg_bytes;
+    out->alg_bytes = pattern == EH_CLIQUE4 ? plan->alg_bytes_k4 : alg;
     out->n_heavy = plan->n_heavy;
     out->n_light = plan->n_light;
     out->kernel_launches = 2;   // the count kernel and the finalize kernel

@@ -96,7 +96,7 @@ struct WorkPlan {
     uint32_t n_light = 0;
     uint32_t *d_heavy_blk = nullptr;   // block layout only: the heavy list, big items first (blocks.cu)
     uint32_t n_big = 0;
-    double alg_bytes = 0;          // algorithmic bytes of one triangle pass
+    double alg_bytes = 0;          // algorithmic bytes of one triangle pass (< 0: not computed yet)
     double alg_bytes_k4 = 0;       // algorithmic bytes of one 4-clique pass
 };
 
@@ -206,6 +206,8 @@ int eh_num_sms();
 
 // Count entry points shared between files.
 eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan **out);
+// the plan's algorithmic bytes of one triangle pass, computed on first use
+eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, double *out);
 // eh_launch_triangle modes: 0 count, 1 lollipop, 2 per-vertex t (d_vt[n]),
 // TRI_MODE_APEX: each work item's triangles in which it is the largest id, to
 // d_vt[item] for heavy items and d_vt[n_heavy + i] for light item i

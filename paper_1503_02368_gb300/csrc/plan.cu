@@ -5,26 +5,45 @@
 
 namespace {
 
-// one warp per vertex: cost(u) = sum_{v in N+(u)} |N+(v)|, and the bytes
-// the method must move for u: A = N+(u) once (its cheaper stored form), then
+// |N+(v)| of every vertex as a compact array (4 bytes a vertex instead of a
+// 32-byte descriptor: the cost pass gathers it once per pair)
+__global__ void k_out_len(const SetDesc *__restrict__ desc, uint32_t n, uint32_t *len) {
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) len[v] = desc[v].len;
+}
+
+// one warp per vertex: cost(u) = sum_{v in N+(u)} |N+(v)|, the order of the
+// work lists (heaviest first)
+__global__ void k_cost(const SetDesc *__restrict__ desc, const uint32_t *__restrict__ nbr,
+                       const uint32_t *__restrict__ len, uint32_t n, uint64_t *cost) {
+    const uint32_t u = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= n) return;
+    const SetDesc du = desc[u];
+    uint64_t c = 0;
+    for (uint32_t j = lane; j < du.len; j += 32) c += __ldg(&len[__ldg(&nbr[du.off + j])]);
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if (lane == 0) cost[u] = c;
+}
+
+// one warp per vertex: the bytes the method must move for u: A = N+(u) once (its cheaper stored form), then
 // per pair (u, v = A[j]) the cheapest way to read what of B = N+(v) can meet
 // A_<v: the uint array (4|B| bytes; at most 32 bytes per probe of the j
 // elements of A_<v when |B| > ratio*j, the galloping side), or the bitset
 // words overlapping A's value range (at most 32 bytes per probe of A_<v).
 // A lower bound on what any of the kernel's dispatch choices reads.
-__global__ void k_cost(TrieView tv, uint32_t n, uint32_t ratio, uint64_t *cost, unsigned long long *bytes_acc) {
+__global__ void k_alg_bytes(TrieView tv, uint32_t n, uint32_t ratio, unsigned long long *bytes_acc) {
     uint32_t u = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (u >= n) return;
     SetDesc du = tv.desc[u];
-    uint64_t c = 0, b = 0;
+    uint64_t b = 0;
     if (du.len >= 2) {
         const uint32_t first = tv.nbr[du.off], last = tv.nbr[du.off + du.len - 1];
         const uint32_t a_lo = (first >> 7) << 2, a_hi = (last >> 5) + 1;   // A's word range
         for (uint32_t j = lane; j < du.len; j += 32) {
             uint32_t v = tv.nbr[du.off + j];
             SetDesc dv = tv.desc[v];
-            c += dv.len;
             if (j == 0 || dv.len == 0) continue;
             uint64_t bb = 4ull * dv.len;
             if ((uint64_t)dv.len > (uint64_t)ratio * j && 32ull * j < bb) bb = 32ull * j;
@@ -39,14 +58,8 @@ __global__ void k_cost(TrieView tv, uint32_t n, uint32_t ratio, uint64_t *cost, 
         }
         if (lane == 0) b += du.nwords && du.nwords < du.len ? 4ull * du.nwords : 4ull * du.len;
     }
-    for (int d = 16; d > 0; d >>= 1) {
-        c += __shfl_xor_sync(0xffffffffu, c, d);
-        b += __shfl_xor_sync(0xffffffffu, b, d);
-    }
-    if (lane == 0) {
-        cost[u] = c;
-        if (b) atomicAdd(bytes_acc, (unsigned long long)b);
-    }
+    for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
+    if (lane == 0 && b) atomicAdd(bytes_acc, (unsigned long long)b);
 }
 
 // class 0: heavy (len > light_max), 1: light (2 <= len <= light_max)
@@ -128,31 +141,53 @@ eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan *
     p.light_max = light_max;
     TrieView tv = t->view();
     uint64_t *cost = nullptr;
-    unsigned long long *bytes_d = nullptr;
+    uint32_t *olen = nullptr;
     EH_TRY(dev_alloc(&cost, t->n, s));
-    eh_status st = dev_alloc(&bytes_d, 1, s);
+    eh_status st = dev_alloc(&olen, t->n, s);
     if (st == EH_OK) {
-        cudaMemsetAsync(bytes_d, 0, 8, s);
-        if (t->n) k_cost<<<(t->n + 7) / 8, 256, 0, s>>>(tv, t->n, 32, cost, bytes_d);
+        if (t->n) {
+            k_out_len<<<(t->n + 255) / 256, 256, 0, s>>>(t->d_desc, t->n, olen);
+            k_cost<<<(t->n + 7) / 8, 256, 0, s>>>(t->d_desc, t->d_onbr, olen, t->n, cost);
+        }
         st = make_list(tv, t->n, t->nb, light_max, 0, cost, s, &p.d_heavy, &p.n_heavy);
     }
     if (st == EH_OK) st = make_list(tv, t->n, t->nb, light_max, 1, cost, s, &p.d_light, &p.n_light);
     if (st == EH_OK && t->d_boff) st = eh_plan_blocks(t, &p, s);
-    unsigned long long bytes_h = 0;
-    if (st == EH_OK) {
-        cudaMemcpyAsync(&bytes_h, bytes_d, 8, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) { eh_set_error("plan: %s", cudaGetErrorString(cudaGetLastError())); st = EH_ECUDA; }
+    if (st == EH_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        eh_set_error("plan: %s", cudaGetErrorString(cudaGetLastError()));
+        st = EH_ECUDA;
     }
     dev_free(cost, s);
-    dev_free(bytes_d, s);
+    dev_free(olen, s);
     if (st != EH_OK) {
         cudaFree(p.d_heavy);
         cudaFree(p.d_light);
         cudaFree(p.d_heavy_blk);
         return st;
     }
-    p.alg_bytes = (double)bytes_h + 8.0 * (double)t->m;
+    p.alg_bytes = -1.0;   // computed on the first request (eh_plan_alg_bytes)
     auto res = t->plans.emplace(light_max, p);
     *out = &res.first->second;
+    return EH_OK;
+}
+
+eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, double *out) {
+    std::lock_guard<std::mutex> g(t->mu);
+    if (p->alg_bytes < 0) {
+        unsigned long long *bytes_d = nullptr, bytes_h = 0;
+        EH_TRY(dev_alloc(&bytes_d, 1, s));
+        eh_status st = EH_OK;
+        if (cudaMemsetAsync(bytes_d, 0, 8, s) != cudaSuccess) st = EH_ECUDA;
+        if (st == EH_OK && t->n) k_alg_bytes<<<(t->n + 7) / 8, 256, 0, s>>>(t->view(), t->n, 32, bytes_d);
+        if (st == EH_OK && (cudaMemcpyAsync(&bytes_h, bytes_d, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                            cudaStreamSynchronize(s) != cudaSuccess)) {
+            eh_set_error("algorithmic bytes: %s", cudaGetErrorString(cudaGetLastError()));
+            st = EH_ECUDA;
+        }
+        dev_free(bytes_d, s);
+        EH_TRY(st);
+        p->alg_bytes = (double)bytes_h + 8.0 * (double)t->m;
+    }
+    *out = p->alg_bytes;
     return EH_OK;
 }

@@ -16,7 +16,11 @@
 // rows.  Inside an item the lanes of a warp take positions from ballot /
 // prefix-sum ranks, stage the round's rows in shared memory and store them
 // as one contiguous run; the warps of a CTA reserve runs from a shared-memory
-// cursor (a device-memory one when an item's rows could pass 2^32).  The
+// cursor (a device-memory one when an item's rows could pass 2^32).  A heavy
+// item's triangle rows are first collected per pair (the third vertices, in a
+// per-warp buffer) and then built and stored 128 at a time, every lane
+// building one row, so a reservation and a store run serve up to 128 rows
+// instead of one round's matches.  The
 // output is dense and the rows of an item fill exactly the range the first
 // pass gave it.  The same 4-clique passes, fed with A = N(x) for the
 // neighbours x of a selected vertex, count the selection query SK4.
@@ -42,6 +46,7 @@ using namespace ehd;
 constexpr uint32_t LIST_WARPS = 8;
 constexpr uint32_t LA_CAP_WORDS = 8192;   // on-chip A: bitmap words or sorted elements (32 KB)
 constexpr uint32_t S_CAP = 512;           // per-warp level-1 set of the 4-clique in shared memory
+constexpr uint32_t TC_CAP = 256;          // per-warp matches of a triangle pair collected before their rows are written
 
 enum { P_TRI = 3, P_K4 = 4 };   // row width
 
@@ -260,7 +265,11 @@ __device__ __forceinline__ void stage_a(const uint32_t *Ag, uint32_t len, uint32
 // the collection of S when listing 4-cliques.  Matches come out in ascending
 // order of w in every branch (rounds walk the sets upwards, lanes in order).
 
-template <int W, bool EMIT, bool COLLECT>
+// BATCH (triangle rows, write pass): the matches are collected like COLLECT
+// and turned into rows by drain(), 128 rows per cursor reservation, every lane
+// building one row, whenever more than TC_CAP - 128 are waiting (a round adds
+// at most 128) and at the end of the pair.
+template <int W, bool EMIT, bool COLLECT, bool BATCH = false>
 struct Level1 {
     const ListArgs &a;
     Sink &sk;
@@ -272,6 +281,7 @@ struct Level1 {
             const uint32_t b = __ballot_sync(FULL, hit);
             if (hit) S[ns + __popc(b & ((1u << (threadIdx.x & 31)) - 1u))] = w;
             ns += __popc(b);
+            if (BATCH && ns > TC_CAP - STAGE_ROWS) drain();
         } else {
             emit_one<W, EMIT>(a, sk, hit, w);
         }
@@ -286,9 +296,22 @@ struct Level1 {
             for (int c = 0; c < 4; ++c)
                 if ((m >> c) & 1u) S[ns + r + i++] = vv[c];
             ns += total;
+            if (BATCH && ns > TC_CAP - STAGE_ROWS) drain();
         } else {
             emit_four<W, EMIT>(a, sk, m, v);
         }
+    }
+    // BATCH: rows (key[0], key[1], S[i]) for the collected matches, then empty S
+    __device__ __forceinline__ void drain() {
+        const uint32_t lane = threadIdx.x & 31;
+        __syncwarp();
+        for (uint32_t c0 = 0; c0 < ns; c0 += STAGE_ROWS) {
+            const uint32_t cn = min(STAGE_ROWS, ns - c0);
+            const unsigned long long base = reserve<EMIT>(sk, cn);
+            for (uint32_t i = lane; i < cn; i += 32) stage_row<W>(a, sk, i, S[c0 + i]);
+            flush<W>(a, sk, base, cn);
+        }
+        ns = 0;
     }
     // A as the on-chip bitmap of words [a_lo, a_lo + a_nw): every element of
     // N+(v) probes it (B's uint array; the padding EH_PAD is out of range)
@@ -372,16 +395,19 @@ __device__ __forceinline__ void k4_level2(const ListArgs &a, Sink &sk, const uin
 
 // Heavy items: a persistent grid, one item per CTA at a time.
 template <int W, bool EMIT>
-__global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
+__global__ void __launch_bounds__(LIST_WARPS * 32, W == P_TRI ? (EMIT ? 4 : 8) : (EMIT ? 6 : 8)) k_list_heavy(ListArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sA = smem;
     __shared__ uint32_t s_item, s_next, s_rel;
     __shared__ unsigned long long s_wcnt[LIST_WARPS];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr bool TBATCH = W == P_TRI && EMIT;   // triangle rows through Level1's BATCH mode
     uint32_t *S = nullptr;
     if (W == P_K4) S = smem + LA_CAP_WORDS + warp * S_CAP;
+    if (TBATCH) S = smem + LA_CAP_WORDS + warp * TC_CAP;
     uint32_t *S_big = a.arena ? a.arena + (uint64_t)(blockIdx.x * LIST_WARPS + warp) * a.arena_stride : nullptr;
-    uint32_t *stage = EMIT ? smem + LA_CAP_WORDS + (W == P_K4 ? LIST_WARPS * S_CAP : 0) + warp * STAGE_ROWS * W
+    uint32_t *stage = EMIT ? smem + LA_CAP_WORDS + (W == P_K4 ? LIST_WARPS * S_CAP : LIST_WARPS * TC_CAP) +
+                                 warp * STAGE_ROWS * W
                            : nullptr;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -418,7 +444,13 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_heavy(ListArgs a) {
             const SetDesc dv = a.tv.desc[v];
             if (dv.len == 0) continue;
             sk.key[1] = __ldg(&a.new2old[v]);
-            if (W == P_TRI) {
+            if (TBATCH) {
+                Level1<P_TRI, EMIT, true, true> l1{a, sk, S, 0};
+                if (st.mode == 0) l1.bitmap(sA, st.a_lo, st.a_nw, dv);
+                else l1.sorted(st.A, j, dv);
+                if (l1.ns) l1.drain();
+                __syncwarp();
+            } else if (W == P_TRI) {
                 Level1<P_TRI, EMIT, false> l1{a, sk, nullptr, 0};
                 if (st.mode == 0) l1.bitmap(sA, st.a_lo, st.a_nw, dv);
                 else l1.sorted(st.A, j, dv);
@@ -499,7 +531,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list_light(ListArgs a) {
 template <int W, bool EMIT>
 eh_status launch_pass(const ListArgs &a, uint32_t heavy_grid, cudaStream_t s) {
     const uint32_t smem = LA_CAP_WORDS * 4 + (W == P_K4 ? LIST_WARPS * S_CAP * 4 : 0) +
-                          (EMIT ? LIST_WARPS * STAGE_ROWS * W * 4 : 0);
+                          (EMIT ? LIST_WARPS * (STAGE_ROWS * W + (W == P_TRI ? TC_CAP : 0)) * 4 : 0);
     EH_CUDA_TRY(cudaFuncSetAttribute(k_list_heavy<W, EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     if (a.n_heavy) k_list_heavy<W, EMIT><<<heavy_grid, LIST_WARPS * 32, smem, s>>>(a);
     EH_CUDA_TRY(cudaGetLastError());

@@ -1,6 +1,6 @@
 // plan.cu -- the per-vertex work list of the pruned trie (cost estimate,
-// light/heavy split by |N+(u)|, heaviest first) and the algorithmic byte
-// count of one triangle pass.
+// light/heavy split by |N+(u)|, heaviest first) and, on request, the
+// algorithmic byte count of one triangle pass.
 #include "eh_internal.cuh"
 
 namespace {
@@ -26,12 +26,13 @@ __global__ void k_cost(const SetDesc *__restrict__ desc, const uint32_t *__restr
     if (lane == 0) cost[u] = c;
 }
 
-// one warp per vertex: the bytes the method must move for u: A = N+(u) once (its cheaper stored form), then
-// per pair (u, v = A[j]) the cheapest way to read what of B = N+(v) can meet
-// A_<v: the uint array (4|B| bytes; at most 32 bytes per probe of the j
-// elements of A_<v when |B| > ratio*j, the galloping side), or the bitset
-// words overlapping A's value range (at most 32 bytes per probe of A_<v).
-// A lower bound on what any of the kernel's dispatch choices reads.
+// one warp per vertex: the bytes the method must move for u: A = N+(u) once
+// (its cheaper stored form), then per pair (u, v = A[j]) the cheapest way to
+// read what of B = N+(v) can meet A_<v: the uint array (4|B| bytes; at most 32
+// bytes per probe of the j elements of A_<v when |B| > ratio*j, the galloping
+// side), or the bitset words overlapping A's value range (at most 32 bytes per
+// probe of A_<v).  A lower bound on what any of the kernel's dispatch choices
+// reads; a reported figure that no count needs, so it runs on request only.
 __global__ void k_alg_bytes(TrieView tv, uint32_t n, uint32_t ratio, unsigned long long *bytes_acc) {
     uint32_t u = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;

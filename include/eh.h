@@ -231,7 +231,10 @@ eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, void *stream
  * (staged sets once per vertex; per intersection the stored layout's bytes
  * of the other set, or 32 bytes per probe on the galloping side; 8 bytes per
  * edge of offsets), the number of heavy (CTA) and light (warp) vertices, and
- * the kernel launches one eh_count_async enqueues. */
+ * the kernel launches one eh_count_async enqueues.  alg_bytes of the triangle
+ * pass (also reported for the lollipop and barbell) is computed by a device
+ * pass on the first call for a plan and cached; the call synchronises
+ * `stream`.  For EH_CLIQUE4 alg_bytes is 0 (not computed). */
 typedef struct {
     double alg_bytes;
     uint64_t n_heavy;

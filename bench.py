@@ -104,12 +104,21 @@ class Clocks:
 
     def start(self, wait_s=3.0):
         """Wait for the sampler's first row, then count only rows written after this call."""
+        self.pre = 0
         if self.p is None:
             return
         t0 = time.time()
         while self._lines() == 0 and self.p.poll() is None and time.time() - t0 < wait_s:
             time.sleep(0.02)
         self.skip = self._lines()
+
+    def mark(self):
+        """The timed region starts: rows written before it (the warm-up's) are
+        kept aside, for a region too short to hold a sample of its own."""
+        if self.p is None:
+            return
+        n = self._lines()
+        self.pre, self.skip = n - self.skip, n
 
     def stop(self):
         if self.p is None:
@@ -120,20 +129,30 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = []
+        rows, warm = [], []
         for i, line in enumerate(open(self.f.name)):
             parts = [x.strip() for x in line.split(",")]
-            if i >= self.skip and len(parts) >= 9:
+            if len(parts) < 9:
+                continue
+            if i >= self.skip:
                 rows.append(parts)
+            elif i >= self.skip - getattr(self, "pre", 0):
+                warm.append(parts)
         os.unlink(self.f.name)
+        note = None
+        if not rows and warm:
+            rows, note = warm[-1:], "no sample fell inside the timed region: the last warm-up sample"
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": 0 if note else len(rows)}
+        if note:
+            out["note"] = note
+        return out
 
 
 def dist_env():
@@ -565,6 +584,8 @@ def run_eh(args):
     out = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    clocks = Clocks(local)   # sampling through the warm-up and the timed region
+    clocks.start()
     for _ in range(args.warmup):
         trie.count_async("triangle", out.data_ptr(), xopts=xo, stream=stream)
     torch.cuda.synchronize()
@@ -572,12 +593,11 @@ def run_eh(args):
     if world > 1:
         torch.distributed.barrier()
 
-    clocks = Clocks(local)
-    clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    clocks.mark()
     for k in range(args.steps):
         flush.fill_(k)                      # L2 flush (256 MiB write) outside the timed interval
         evs[k][0].record(stream)

@@ -43,6 +43,7 @@ def run_sampler(monkeypatch, tmp_path, cap):
     import bench
     c = bench.Clocks(0)
     c.start()
+    c.mark()
     time.sleep(0.7)
     return c.stop()
 
@@ -60,11 +61,29 @@ def test_active_throttle_reason_reported(monkeypatch, tmp_path):
     assert r["sm_mhz"] == 2070.0
 
 
+def test_region_without_a_sample_falls_back_to_the_warm_up(monkeypatch, tmp_path):
+    d, _ = make_fake(tmp_path, "Not Active")
+    monkeypatch.setenv("PATH", d + os.pathsep + os.environ.get("PATH", ""))
+    monkeypatch.setenv("CAP", "Not Active")
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    c.start()            # the first row (hw_slowdown) is before the warm-up
+    time.sleep(0.5)      # warm-up rows under load
+    c.p.terminate()      # no row inside the timed region
+    c.p.wait()
+    c.mark()
+    r = c.stop()
+    assert r["samples"] == 0 and "warm-up" in r["note"]
+    assert r["sm_mhz"] == 2070.0 and r["reasons"] == []
+
+
 def test_missing_sampler(monkeypatch, tmp_path):
     monkeypatch.setenv("PATH", str(tmp_path))
     sys.path.insert(0, ROOT)
     import bench
     c = bench.Clocks(0)
     c.start()
+    c.mark()
     r = c.stop()
     assert r["sm_mhz"] is None

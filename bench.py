@@ -325,7 +325,11 @@ def bench_clique4(eh, reps=5):
     trie.close()
     return {"workload": "chunglu_n1000000_g2.1 (w_max 5e4, mean degree 40) 4-clique", "m_unique_edges": m,
             "count": c, "exact_vs_oracle": c == gold["clique4"], "ms": ms, "edges_per_s": m / (ms / 1e3),
-            "cliques_per_s": c / (ms / 1e3), "tau": 256, "cta_warps": 16,
+            "cliques_per_s": c / (ms / 1e3),
+            "intersections_per_s": (m + int(gold.get("triangle", 0))) / (ms / 1e3),
+            "intersections": "level 1: one per pruned edge (x, y); level 2: one per z in S_xy, i.e. one per "
+                             "triangle (the oracle's count)",
+            "tau": 256, "cta_warps": 16,
             "barbell": {"count": cb, "exact_vs_oracle": cb == gold.get("barbell"), "ms": ms_b,
                         "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"},
             "selection": sel}
@@ -667,6 +671,7 @@ def run_eh(args):
         lo_bytes = info["alg_bytes"] + 4.0 * g["n"]
         extra["lollipop"] = {"workload": WORKLOAD.replace("triangle", "lollipop (join semantics)"),
                              "count": int(lo_out.item()), "ms": min(lo_ms),
+                             "intersections_per_s": m / (min(lo_ms) / 1e3),   # one per pruned edge
                              "achieved_gbs": lo_bytes / (min(lo_ms) / 1e3) / 1e9,
                              "frac_of_measured_hbm": lo_bytes / (min(lo_ms) / 1e3) / 1e9 / hbm,
                              "alg_bytes": lo_bytes,

@@ -173,6 +173,14 @@ def reduce_max(x, world, device=None):
     return float(t.item())
 
 
+def step_stats(step_ms):
+    """Per-step times: min, median, max, and the paper's protocol (Sec. 5.1.3):
+    the fastest and slowest runs dropped, the rest averaged."""
+    srt = sorted(step_ms)
+    return {"min": srt[0], "median": statistics.median(srt), "max": srt[-1],
+            "trimmed_mean": statistics.mean(srt[1:-1] if len(srt) > 2 else srt)}
+
+
 def aggregate(edges_per_rank, ms_per_rank_max, world):
     """Whole-job throughput: all ranks' edges over the slowest rank's time."""
     return world * edges_per_rank / (ms_per_rank_max / 1e3)
@@ -700,10 +708,7 @@ def run_eh(args):
                            "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps,
-                "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms),
-                            # the paper's protocol (Sec. 5.1.3): drop the fastest and slowest run, average the rest
-                            "trimmed_mean": (statistics.mean(sorted(step_ms)[1:-1]) if len(step_ms) > 2
-                                             else statistics.mean(step_ms))}}
+                "step_ms": step_stats(step_ms)}
         line.update(extra)
         print(json.dumps(line), flush=True)
     trie.close()

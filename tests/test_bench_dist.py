@@ -44,3 +44,12 @@ def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max(3.5, 1) == 3.5
     assert bench.aggregate(10.0, 1000.0, 1) == 10.0
+
+
+def test_step_stats():
+    import bench
+    st = bench.step_stats([10.0, 9.0, 30.0, 11.0, 10.0, 9.5, 1.0])
+    assert st["min"] == 1.0 and st["max"] == 30.0 and st["median"] == 10.0
+    assert abs(st["trimmed_mean"] - (9.0 + 9.5 + 10.0 + 10.0 + 11.0) / 5) < 1e-12
+    assert bench.step_stats([4.0, 6.0])["trimmed_mean"] == 5.0
+    assert bench.step_stats([7.0])["trimmed_mean"] == 7.0

@@ -10,9 +10,17 @@ creation) is outside the step, as in the paper's timing rule (Sec. 5.1.3);
 the end-to-end figure (`e2e`) includes it, with the host edge list copied in
 and the count copied out inside the timed region.
 
-N > 1 (torchrun): every rank counts its own replica of the graph
-(independent problems, no collective on the data path); the value is the
-edges of all replicas over the slowest rank's time.
+N > 1 (torchrun): every rank holds a replica of the trie and counts its part
+of the work (eh_count_range_async: the heavy and light work lists cut into
+N contiguous cost-balanced ranges); one 8-byte all-reduce sums the parts.  A
+step is one whole-graph count on all ranks together (strong scaling); the
+value is the graph's edges over the slowest rank's step time.
+
+With no --workload the line also carries every other workload as extra keys:
+the ER triangle count, the R-MAT-22 lollipop, the Chung-Lu 4-clique (with
+the barbell and the selection queries), the 4,096-query batch against one
+launch per query, and the R-MAT-24 serving loop, each with its own clock
+record and exactness check.
 
 The reference arm is the CPU oracle (plain nested-loop generic join) timed
 on a bounded sample of the outer loop of the same workload.
@@ -46,8 +54,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="triangle", choices=["triangle", "clique4", "batch", "serve", "list", "order", "all"],
-                    help="triangle: the headline line; batch/serve/all add the query-batch and serving results")
+    ap.add_argument("--workload", default="default",
+                    choices=["default", "triangle", "er", "lollipop", "clique4", "batch", "serve", "list", "order", "all"],
+                    help="default: the headline line plus every workload (ER triangle, R-MAT-22 lollipop, Chung-Lu "
+                         "4-clique, query batch, serving) as extra keys; triangle: the headline only; all: default "
+                         "plus the listing and the ordering study; any other name: the headline plus that leg")
     ap.add_argument("--serve-queries", type=int, default=1500)
     return ap.parse_args()
 
@@ -173,12 +184,65 @@ def reduce_max(x, world, device=None):
     return float(t.item())
 
 
+def sum_over_ranks_(t, world):
+    """In-place sum of a rank's partial count tensor over all ranks (the one
+    8-byte exchange of a partitioned count); identity on one rank."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t)
+    return t
+
+
+def part_count_host(cost, per_item, part, nparts):
+    """A rank's share of a list under eh_range_bounds' split: the sum of
+    per_item over its range of items (host arrays; the multi-rank test's
+    stand-in for the device count of that range)."""
+    import paper_1503_02368_gb300 as eh
+    lo, hi = eh.range_bounds(cost, part, nparts)
+    return int(per_item[lo:hi].sum())
+
+
 def step_stats(step_ms):
     """Per-step times: min, median, max, and the paper's protocol (Sec. 5.1.3):
     the fastest and slowest runs dropped, the rest averaged."""
     srt = sorted(step_ms)
     return {"min": srt[0], "median": statistics.median(srt), "max": srt[-1],
             "trimmed_mean": statistics.mean(srt[1:-1] if len(srt) > 2 else srt)}
+
+
+def timed_steps(fn, steps, warmup, stream, flush, clocks=None):
+    """fn() `warmup` times untimed, then `steps` times, each bracketed by CUDA
+    events on `stream` with the L2 flushed before it (a write larger than L2,
+    outside the events).  `clocks` (a started Clocks) is marked at the start of
+    the timed region and stopped after it.  Returns (per-step ms, clocks)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if clocks is not None:
+        clocks.mark()
+    for k in range(steps):
+        flush.fill_(k)
+        evs[k][0].record(stream)
+        fn()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    return [a.elapsed_time(b) for a, b in evs], clk
+
+
+def roofline(alg_bytes, ms, kernel, note=None):
+    """HBM roofline of one launch: algorithmic bytes over the measured time
+    against the measured copy bandwidth."""
+    hbm, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    r = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+         "kernel": kernel}
+    if note:
+        r["note"] = note
+    return r
 
 
 def aggregate(edges_per_rank, ms_per_rank_max, world):
@@ -241,9 +305,10 @@ def cpu_baseline(g, seconds, seed=7):
                                         % (v_one, e_one, t_one)}}
 
 
-def bench_batch(eh, tau=32, reps=3, log=None):
+def bench_batch(eh, local, tau=32, reps=3):
     """4,096 triangle/4-clique queries on R-MAT-20 ego nets: one persistent batch
-    vs one query at a time (same kernels); counts must agree exactly."""
+    vs one query at a time (same kernels); counts must agree exactly, and the
+    oracle's sampled queries must match."""
     import numpy as np
     import torch
     from synth import workloads as W
@@ -255,69 +320,144 @@ def bench_batch(eh, tau=32, reps=3, log=None):
         tau = best["tau"]
     xo = eh.exec_opts(cta_warps=best["cta_warps"], light_max=best["light_max"]) if best else None
     trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
-    c0, s0 = trie.count_batch(pats, g["offsets"], g["pool"], mode=0, xopts=xo)
+    c0, s0 = trie.count_batch(pats, g["offsets"], g["pool"], mode=0, xopts=xo)      # warm-up
     torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    clk.mark()
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
         c, st = trie.count_batch(pats, g["offsets"], g["pool"], mode=0, xopts=xo)
         torch.cuda.synchronize()
         ts.append(time.perf_counter() - t0)
+    clocks = clk.stop()
+    clk = Clocks(local)
+    clk.start()
+    clk.mark()
     t0 = time.perf_counter()
     c1, s1 = trie.count_batch(pats, g["offsets"], g["pool"], mode=1, xopts=xo)
     torch.cuda.synchronize()
     t_one = time.perf_counter() - t0
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json"))).get("rmat_s20_ego4096")
-    exact = None
-    if gold:
-        exact = all(int(c0[int(q)]) == v["count"] for q, v in gold["queries"].items())
-    ok = bool(np.array_equal(c0, c) and np.array_equal(c0, c1) and not s0.any() and not s1.any())
+    clocks_one = clk.stop()
+    gold = golden("rmat_s20_ego4096")
+    exact = all(int(c0[int(q)]) == v["count"] for q, v in gold["queries"].items())
+    same = bool(np.array_equal(c0, c) and np.array_equal(c0, c1) and not s0.any() and not s1.any())
     trie.close()
     nq = len(pats)
     return {"workload": "rmat_s20_ef16 + 4096 ego nets |S| log-uniform 64..65536, triangle/4-clique alternating",
             "queries": nq, "subset_ids": int(len(g["pool"])), "tau": tau,
             "exec": {"cta_warps": best["cta_warps"], "light_max": best["light_max"]} if best else "defaults",
-            "batched_qps": nq / min(ts), "batched_s": min(ts), "one_launch_per_query_qps": nq / t_one,
-            "one_launch_per_query_s": t_one, "speedup": t_one / min(ts), "same_counts": ok,
-            "exact_vs_oracle_sample": exact,
+            "batched_qps": nq / min(ts), "batched_s": min(ts), "batched_s_all": ts,
+            "one_launch_per_query_qps": nq / t_one, "one_launch_per_query_s": t_one, "speedup": t_one / min(ts),
+            "same_counts": same, "exact": bool(exact and same), "exact_queries_checked": len(gold["queries"]),
+            "clocks": clocks, "clocks_one_per_query": clocks_one,
             "timing": "host wall clock around eh_count_batch (host subsets in, counts out), best of %d" % reps}
 
 
-def bench_clique4(eh, reps=5):
-    """Whole-graph 4-clique count on the Chung-Lu graph (n = 1e6, ~2e7 edges, gamma 2.1)."""
+def golden(name):
+    return json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))[name]
+
+
+def bench_er(eh, local, steps=500, warmup=5):
+    """Whole-graph triangle count on Erdos-Renyi G(n=10,000, m=100,000).  The
+    trie (about 0.8 MB) fits L2 many times over; L2 is flushed before each
+    timed count all the same, so each count starts from DRAM."""
+    import torch
+    from synth import workloads as W
+    g = W.er_10k_100k()
+    gold = golden("er_n10000_m100000")
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    m = trie.stats()["n_edges"]
+    info = trie.info("triangle")
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clk = Clocks(local)
+    clk.start()
+    ms, clocks = timed_steps(lambda: trie.count_async("triangle", out.data_ptr(), stream=stream), steps, warmup,
+                             stream, flush, clk)
+    trie.status(stream)
+    c = int(out.item())
+    t = statistics.mean(ms)
+    trie.close()
+    return {"workload": "er_n10000_m100000 triangle: Erdos-Renyi G(n=10,000, m=100,000), seed 1504",
+            "m_unique_edges": m, "count": c, "exact": c == gold["triangle"], "ms": t,
+            "edges_per_s": m / (t / 1e3), "steps": steps, "step_ms": step_stats(ms),
+            "roofline": roofline(info["alg_bytes"], t, "k_triangle<0,8>",
+                                 "the whole trie is L2-resident after the first touch; DRAM-cold start per count"),
+            "clocks": clocks, "timing": "CUDA events per count, L2 flushed before each (outside the events)"}
+
+
+def bench_lollipop(eh, local, trie, xo, info, m, steps=10):
+    """Whole-graph lollipop count (join semantics) on the resident R-MAT-22
+    trie: the triangle traversal, each triangle adding its vertices' degrees."""
+    import numpy as np
+    import torch
+    gold = golden("rmat_s22_ef16")
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clk = Clocks(local)
+    clk.start()
+    ms, clocks = timed_steps(lambda: trie.count_async("lollipop", out.data_ptr(), xopts=xo, stream=stream), steps,
+                             3, stream, flush, clk)
+    trie.status(stream)
+    c = int(out.item())
+    t = statistics.mean(ms)
+    if "lollipop" in gold:
+        exact, how = c == gold["lollipop"], "equal to the oracle's count"
+    else:
+        # no oracle count at this size: the per-vertex identity L = sum_x 2 t(x) d(x) with t(x)
+        # from the per-vertex kernel, whose sampled values are the oracle's
+        vt = trie.vertex_triangles()
+        ok_t = all(int(vt[int(v)]) == tv for v, tv in gold["vertex_triangles"].items())
+        ex = trie.export(1)
+        d_old = np.zeros(len(ex["len"]), np.uint64)
+        d_old[ex["new_to_old"]] = ex["len"]
+        exact = ok_t and c == int((2 * vt.astype(object) * d_old.astype(object)).sum())
+        how = "sum_x 2 t(x) d(x) with t(x) checked at the oracle's sampled vertices"
+    return {"workload": WORKLOAD.replace("triangle", "lollipop (join semantics)"), "count": c, "exact": bool(exact),
+            "exact_how": how, "ms": t, "step_ms": step_stats(ms), "vs_triangle": None,
+            "intersections_per_s": m / (t / 1e3),
+            "roofline": roofline(info["alg_bytes"], t, "k_triangle<1,%d>" % xo.cta_warps,
+                                 "the triangle traversal's algorithmic bytes (the degrees are 4 bytes a vertex "
+                                 "more, read once per staged set)"),
+            "clocks": clocks, "timing": "CUDA events per count, L2 flushed before each (outside the events)"}
+
+
+def bench_clique4(eh, local, reps=10):
+    """Whole-graph 4-clique count on the Chung-Lu graph (n = 1e6, ~2e7 edges,
+    gamma 2.1), CUDA events per count with L2 flushed before each, roofline on
+    the 4-clique algorithmic bytes; then the barbell by its two-node GHD plan
+    and the selection queries on the same trie."""
+    import numpy as np
     import torch
     from synth import workloads as W
     g = W.chunglu_1m()
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))["chunglu_n1000000_g2.1"]
+    gold = golden("chunglu_n1000000_g2.1")
     trie = eh.Trie(g["src"], g["dst"], g["n"], tau=256)
     m = trie.stats()["n_edges"]
-    out = torch.zeros(1, dtype=torch.int64, device="cuda")
     xo = eh.exec_opts(cta_warps=16)
-    for _ in range(2):
-        trie.count_async("clique4", out.data_ptr(), xopts=xo)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record()
-    for _ in range(reps):
-        trie.count_async("clique4", out.data_ptr(), xopts=xo)
-    s1.record()
-    torch.cuda.synchronize()
-    trie.status()
-    ms = s0.elapsed_time(s1) / reps
+    info = trie.info("clique4", xopts=xo)
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clk = Clocks(local)
+    clk.start()
+    ms, clocks = timed_steps(lambda: trie.count_async("clique4", out.data_ptr(), xopts=xo, stream=stream), reps, 2,
+                             stream, flush, clk)
+    trie.status(stream)
     c = int(out.item())
+    t = statistics.mean(ms)
     # the barbell by its two-node GHD plan on the same graph (per-vertex triangles, then the edge join)
-    trie.count_async("barbell", out.data_ptr())
-    torch.cuda.synchronize()
-    s0.record()
-    for _ in range(reps):
-        trie.count_async("barbell", out.data_ptr())
-    s1.record()
-    torch.cuda.synchronize()
-    trie.status()
-    ms_b = s0.elapsed_time(s1) / reps
+    clk = Clocks(local)
+    clk.start()
+    ms_b, clocks_b = timed_steps(lambda: trie.count_async("barbell", out.data_ptr(), stream=stream), 5, 1, stream,
+                                 flush, clk)
+    trie.status(stream)
     cb = int(out.item())
     # selection queries (Sec. 5.3) with the selected vertex = the 1000th-highest degree
-    import numpy as np
     deg = np.zeros(g["n"], np.int64)
     np.add.at(deg, g["src"], 1)
     np.add.at(deg, g["dst"], 1)
@@ -332,13 +472,18 @@ def bench_clique4(eh, reps=5):
     sel["timing"] = "host clock around one synchronous eh_count_selected"
     trie.close()
     return {"workload": "chunglu_n1000000_g2.1 (w_max 5e4, mean degree 40) 4-clique", "m_unique_edges": m,
-            "count": c, "exact_vs_oracle": c == gold["clique4"], "ms": ms, "edges_per_s": m / (ms / 1e3),
-            "cliques_per_s": c / (ms / 1e3),
-            "intersections_per_s": (m + int(gold.get("triangle", 0))) / (ms / 1e3),
+            "count": c, "exact": c == gold["clique4"], "ms": t, "step_ms": step_stats(ms),
+            "edges_per_s": m / (t / 1e3), "cliques_per_s": c / (t / 1e3),
+            "intersections_per_s": (m + int(gold.get("triangle", 0))) / (t / 1e3),
             "intersections": "level 1: one per pruned edge (x, y); level 2: one per z in S_xy, i.e. one per "
                              "triangle (the oracle's count)",
             "tau": 256, "cta_warps": 16,
-            "barbell": {"count": cb, "exact_vs_oracle": cb == gold.get("barbell"), "ms": ms_b,
+            "roofline": roofline(info["alg_bytes"], t, "k_clique4<16>",
+                                 "4-clique algorithmic bytes: level 1 as the triangle pass, level 2 the pairs "
+                                 "(S_<z, N+(z)), S spills of more than 512 elements written and read"),
+            "clocks": clocks, "timing": "CUDA events per count, L2 flushed before each (outside the events)",
+            "barbell": {"count": cb, "exact": cb == gold.get("barbell"), "ms": statistics.mean(ms_b),
+                        "step_ms": step_stats(ms_b), "clocks": clocks_b,
                         "plan": "GHD: per-vertex triangle counts, then the U(x,x') join on the aggregates"},
             "selection": sel}
 
@@ -451,13 +596,11 @@ def bench_order(eh, n=1 << 20, n_pairs=8_000_000, reps=3):
     return res
 
 
-def bench_serve(eh, n_queries=1500, tau=32, log=None):
+def bench_serve(eh, local, n_queries=1500, tau=32):
     """Resident R-MAT-24; ego-net queries (induced edges log-uniform 100..1e6),
     patterns uniform over triangle / 4-clique / lollipop; closed-loop saturation,
     then Poisson arrivals at 0.5x, 0.8x, 1.0x of it; p50/p99 latency."""
-    import threading
     import numpy as np
-    import torch
     from synth import workloads as W
     g = W.rmat24_serve(n_queries=n_queries)
     names = ("triangle", "clique4", "lollipop")
@@ -492,30 +635,60 @@ def bench_serve(eh, n_queries=1500, tau=32, log=None):
         srv.close()
         return out, lat, t_end, st
 
+    run([0.0] * min(64, n_queries))                      # warm-up (kernels loaded, pool warmed)
+    clk = Clocks(local)
+    clk.start()
+    clk.mark()
     out, lat, span, st = run([0.0] * n_queries)          # saturation (closed loop)
+    res["saturation_clocks"] = clk.stop()
     sat = n_queries / span
     res["saturation_qps"] = sat
     res["saturation_mean_batch"] = st["mean_batch"]
     counts = [c for c, _ in out]
     ok_status = all(s_ == 0 for _, s_ in out)
-    # each result equals the query alone
+    # each result equals the query alone, and the oracle's sampled queries
     rng = np.random.default_rng(0)
     sample = rng.choice(n_queries, size=min(64, n_queries), replace=False)
     alone_ok = all(trie.count(pats[q], subset=subsets[q]) == counts[q] for q in sample)
     res["same_alone_and_in_mix"] = bool(alone_ok and ok_status)
+    gold = golden("rmat_s24_serve")
+    gq = {int(q): v for q, v in gold["queries"].items() if int(q) < n_queries}
+    res["exact_vs_oracle_sample"] = all(counts[q] == v["count"] and pats[q] == v["pattern"] for q, v in gq.items())
+    res["exact_queries_checked"] = len(gq)
     res["open_loop"] = []
+    same_all = True
     for frac in (0.5, 0.8, 1.0):
         lam = frac * sat
         gaps = rng.exponential(1.0 / lam, size=n_queries)
         arr = np.cumsum(gaps) - gaps[0]
+        clk = Clocks(local)
+        clk.start()
+        clk.mark()
         out2, lat2, span2, st2 = run(list(arr))
+        clocks = clk.stop()
         same = [c for c, _ in out2] == counts
+        same_all &= same
         res["open_loop"].append({"rate_qps": lam, "achieved_qps": n_queries / span2,
                                  "p50_ms": 1e3 * float(np.percentile(lat2, 50)),
                                  "p99_ms": 1e3 * float(np.percentile(lat2, 99)),
-                                 "mean_batch": st2["mean_batch"], "same_counts": same})
+                                 "mean_batch": st2["mean_batch"], "same_counts": same, "clocks": clocks})
+    res["exact"] = bool(res["same_alone_and_in_mix"] and res["exact_vs_oracle_sample"] and same_all)
     trie.close()
     return res
+
+
+def headline_config(n, m, world):
+    """The headline workload's config (both arms): graph, layout and launch knobs."""
+    from paper_1503_02368_gb300 import autotune
+    tuned = autotune.load("rmat_s22_triangle")
+    return {"workload": WORKLOAD, "n_vertices": n, "m_unique_edges": m,
+            "tau": tuned["tau"] if tuned else 32, "cta_warps": tuned["cta_warps"] if tuned else 8,
+            "light_max": tuned["light_max"] if tuned else 32, "gallop_ratio": tuned.get("gallop_ratio", 32) if tuned else 32,
+            "tuning": "autotuned (paper_1503_02368_gb300/tuned.json)" if tuned else "fixed",
+            "l2": "flushed between timed steps (256 MiB write, outside the events)",
+            "parallelism": "1 GPU" if world == 1 else
+            "count partitioned over %d GPUs (replicated trie, cost-balanced work ranges, one 8-byte all-reduce)"
+            % world}
 
 
 def run_reference(args):
@@ -554,85 +727,86 @@ def run_reference(args):
     value = tot_e / tot_t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n_vertices": g["n"],
-                                              "sample_outer_vertices_per_step": k},
+            "higher_is_better": True, "scaling": "weak" if world == 1 else "strong", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic", "config": headline_config(g["n"], G.m, max(world, args.gpus)),
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d random outer-loop vertices per step of %d; adjacency build %.1f s "
-                                       "excluded" % (k, g["n"], build_s)},
+                             "sample": "%d random outer-loop vertices per step of %d (the pruned edges they own "
+                                       "counted); adjacency build %.1f s excluded" % (k, g["n"], build_s)},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
 
 
 def run_eh(args):
-    import numpy as np
     import torch
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     import paper_1503_02368_gb300 as eh
     from synth import workloads as W
 
-    from paper_1503_02368_gb300 import autotune
     g = W.rmat22()
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "workload_counts.json")))["rmat_s22_ef16"]
-    tuned = autotune.load("rmat_s22_triangle")
-    tau = args.tau if args.tau is not None else (tuned["tau"] if tuned else 32)
-    warps = tuned["cta_warps"] if tuned and args.tau is None else 8
-    light_max = tuned["light_max"] if tuned and args.tau is None else 32
-    ratio = tuned.get("gallop_ratio", 32) if tuned and args.tau is None else 32
+    gold = golden("rmat_s22_ef16")
+    cfg0 = headline_config(g["n"], None, world)
+    tau = args.tau if args.tau is not None else cfg0["tau"]
+    fixed = args.tau is not None and args.tau != cfg0["tau"]
+    warps = 8 if fixed else cfg0["cta_warps"]
+    light_max = 32 if fixed else cfg0["light_max"]
+    ratio = 32 if fixed else cfg0["gallop_ratio"]
     xo = eh.exec_opts(cta_warps=warps, light_max=light_max, gallop_ratio=ratio)
-    args.tau = tau
     trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
-    st = trie.stats()
-    m = st["n_edges"]
+    m = trie.stats()["n_edges"]
     info = trie.info("triangle", xopts=xo)
     stream = torch.cuda.current_stream()
     out = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    if world == 1:
+        def step():
+            trie.count_async("triangle", out.data_ptr(), xopts=xo, stream=stream)
+    else:
+        # one graph per step: this rank's share of the work ranges, then the 8-byte sum
+        def step():
+            trie.count_range_async("triangle", rank, world, out.data_ptr(), xopts=xo, stream=stream)
+            sum_over_ranks_(out, world)
+
     clocks = Clocks(local)   # sampling through the warm-up and the timed region
     clocks.start()
     for _ in range(args.warmup):
-        trie.count_async("triangle", out.data_ptr(), xopts=xo, stream=stream)
+        step()
     torch.cuda.synchronize()
     trie.status(stream)
     if world > 1:
-        torch.distributed.barrier()
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        dist.barrier()
     torch.cuda.synchronize()
+    step_ms, clk = timed_steps(step, args.steps, 0, stream, flush, clocks)
     if world > 1:
-        torch.distributed.barrier()
-    clocks.mark()
-    for k in range(args.steps):
-        flush.fill_(k)                      # L2 flush (256 MiB write) outside the timed interval
-        evs[k][0].record(stream)
-        trie.count_async("triangle", out.data_ptr(), xopts=xo, stream=stream)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
+        dist.barrier()
     trie.status(stream)
     count = int(out.item())
     exact = count == gold["triangle"]
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     ms_max = reduce_max(ms, world, dev)
-    value = aggregate(m, ms_max, world)
+    value = m / (ms_max / 1e3)          # one whole graph per step, on all ranks together
 
-    hbm, peak_kind = measured_peaks()
-    achieved = info["alg_bytes"] / (ms / 1e3) / 1e9
-    traffic = profile_traffic(os.path.join(ROOT, "paper_1503_02368_gb300", "csrc", "count.cu"))
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
-            "alg_bytes_per_launch": info["alg_bytes"], "kernel": "k_triangle<0,%d>" % warps}
+    roof = roofline(info["alg_bytes"], ms, "k_triangle<0,%d>" % warps)
+    roof["traffic"] = profile_traffic(os.path.join(ROOT, "paper_1503_02368_gb300", "csrc", "count.cu"))
+    hbm = roof["peak"]
+    st_ach = info["alg_bytes_stored"] / (ms / 1e3) / 1e9
+    roof["stored_layout"] = {"achieved": round(st_ach, 1), "frac": round(st_ach / hbm, 4),
+                             "alg_bytes_per_launch": info["alg_bytes_stored"],
+                             "definition": "every set at its stored layout's size (4|S| uint, 4 x words bitset), "
+                                           "N+(u) once per u, N+(v) once per pair (at most 32 B per element of "
+                                           "N+(u) past the 32:1 ratio), 8 B per edge"}
+    roof["definition"] = ("lower bound over the stored layouts: N+(u) once in its cheaper form, per pair the "
+                          "cheapest read of what of N+(v) can meet N+(u)_<v, 8 B per edge")
+    if world > 1:
+        roof["note"] = "per rank: the whole graph's bytes over the partitioned step's time"
 
     e2e = None
     if not args.no_e2e:
@@ -641,79 +815,80 @@ def run_eh(args):
         dst_p = torch.from_numpy(g["dst"]).pin_memory()
         ns, nd = src_p.numpy(), dst_p.numpy()
         e2e_steps = max(2, min(5, args.steps))
-        eh.Trie(ns, nd, g["n"], tau=tau).count("triangle", xopts=xo)     # warm-up
+
+        def e2e_step():
+            t = eh.Trie(ns, nd, g["n"], tau=tau)
+            if world == 1:
+                c = t.count("triangle", xopts=xo)
+            else:
+                t.count_range_async("triangle", rank, world, out.data_ptr(), xopts=xo, stream=stream)
+                c = int(sum_over_ranks_(out, world).item())
+                t.status(stream)
+            t.close()
+            return c
+
+        e2e_step()     # warm-up
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         ok = True
         for _ in range(e2e_steps):
-            t = eh.Trie(ns, nd, g["n"], tau=tau)
-            ok &= t.count("triangle", xopts=xo) == gold["triangle"]
-            t.close()
+            ok &= e2e_step() == gold["triangle"]
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
         e2e_ms = reduce_max(e2e_ms, world, dev)
-        e2e = {"value": aggregate(m, e2e_ms, world), "unit": "edges/s", "ms_per_step": e2e_ms,
+        e2e = {"value": m / (e2e_ms / 1e3), "unit": "edges/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": int(ns.nbytes + nd.nbytes), "d2h_bytes_per_step": 8, "exact": bool(ok),
                "includes": "H2D of the raw edge list, trie build (sort, dedup, ordering, layouts), work plan, "
-                           "count, D2H of the count, trie release"}
+                           "count%s, D2H of the count, trie release" % (" (this rank's range + all-reduce)"
+                                                                         if world > 1 else "")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, args.cpu_seconds)
 
+    legs = {"default": ("er", "lollipop", "clique4", "batch", "serve"),
+            "all": ("er", "lollipop", "clique4", "batch", "serve", "list", "order"),
+            "triangle": ()}.get(args.workload, (args.workload,))
     extra = {}
-    if rank == 0 and args.workload in ("clique4", "all"):
-        # lollipop on the same trie: the triangle traversal plus a degree gather per match
-        lo_out = torch.zeros(1, dtype=torch.int64, device=dev)
-        trie.count_async("lollipop", lo_out.data_ptr(), xopts=xo, stream=stream)
-        lo_ms = []
-        for k in range(3):
-            flush.fill_(k)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            trie.count_async("lollipop", lo_out.data_ptr(), xopts=xo, stream=stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            lo_ms.append(a.elapsed_time(b))
-        trie.status(stream)
-        lo_bytes = info["alg_bytes"] + 4.0 * g["n"]
-        extra["lollipop"] = {"workload": WORKLOAD.replace("triangle", "lollipop (join semantics)"),
-                             "count": int(lo_out.item()), "ms": min(lo_ms),
-                             "intersections_per_s": m / (min(lo_ms) / 1e3),   # one per pruned edge
-                             "achieved_gbs": lo_bytes / (min(lo_ms) / 1e3) / 1e9,
-                             "frac_of_measured_hbm": lo_bytes / (min(lo_ms) / 1e3) / 1e9 / hbm,
-                             "alg_bytes": lo_bytes,
-                             "exact": "checked against the oracle's per-vertex identity in the GPU tests"}
-    if rank == 0 and args.workload in ("order", "all"):
-        extra["order"] = bench_order(eh)
-    if rank == 0 and args.workload in ("list", "all"):
-        extra["list"] = bench_list(eh, trie, xo, info["alg_bytes"], gold)
-    if rank == 0 and args.workload in ("clique4", "batch", "all"):
-        extra["clique4"] = bench_clique4(eh)
-    if rank == 0 and args.workload in ("batch", "all"):
-        extra["batch"] = bench_batch(eh)
-    if rank == 0 and args.workload in ("serve", "all"):
-        extra["serve"] = bench_serve(eh, args.serve_queries)
+    if world == 1:
+        for leg in legs:
+            if leg == "er":
+                extra["er"] = bench_er(eh, local)
+            elif leg == "lollipop":
+                extra["lollipop"] = bench_lollipop(eh, local, trie, xo, info, m)
+                extra["lollipop"]["vs_triangle"] = extra["lollipop"]["ms"] / ms
+            elif leg == "list":
+                extra["list"] = bench_list(eh, trie, xo, info["alg_bytes"], gold)
+            elif leg == "order":
+                extra["order"] = bench_order(eh)
+            elif leg == "clique4":
+                extra["clique4"] = bench_clique4(eh, local)
+            elif leg == "batch":
+                extra["batch"] = bench_batch(eh, local)
+            elif leg == "serve":
+                extra["serve"] = bench_serve(eh, local, args.serve_queries)
 
     if rank == 0:
+        cfg = headline_config(g["n"], m, world)
+        cfg.update({"tau": tau, "cta_warps": warps, "light_max": light_max, "gallop_ratio": ratio})
+        if fixed:
+            cfg["tuning"] = "fixed"
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_vertices": g["n"], "m_unique_edges": m, "tau": tau,
-                           "cta_warps": warps, "light_max": light_max, "gallop_ratio": ratio,
-                           "tuning": "autotuned (paper_1503_02368_gb300/tuned.json)" if tuned and tau == tuned["tau"]
-                           else "fixed",
-                           "count": count, "exact_vs_oracle": exact,
-                           "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                           "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+                "scaling": "weak" if world == 1 else "strong", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic", "config": cfg, "count": count, "exact": exact,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps,
                 "step_ms": step_stats(step_ms)}
+        if extra:
+            line["exact_all"] = bool(exact and all(v.get("exact", True) for v in extra.values()))
         line.update(extra)
         print(json.dumps(line), flush=True)
     trie.close()
     if world > 1:
-        torch.distributed.destroy_process_group()
+        dist.destroy_process_group()
 
 
 def main():

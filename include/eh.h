@@ -147,7 +147,10 @@ typedef struct {
 #define EH_EXEC_SORTED_A 1u /* never a bitmap: the sorted array (on chip when it fits) */
 #define EH_EXEC_GLOBAL_A 2u /* A read from device memory, not staged */
 
-typedef struct {
+/* Facts of a built trie.  The struct tag is the name of the call that fills
+ * it (eh_trie_stats), so C and C++ code names the type `struct eh_trie_stats`
+ * or `eh_trie_stats_t`. */
+struct eh_trie_stats {
     uint32_t n_vertices;   /* id space */
     uint32_t n_active;     /* vertices with degree > 0 */
     uint64_t n_edges;      /* unique undirected edges m */
@@ -160,7 +163,8 @@ typedef struct {
     uint64_t device_bytes;   /* device memory held by the trie */
     uint32_t bitset_tau;
     uint32_t reserved;
-} eh_trie_stats;
+};
+typedef struct eh_trie_stats eh_trie_stats_t;
 
 /* One query of a batch: pattern over the subgraph induced by
  * subset_pool[subset_off .. subset_off+subset_len) (original ids; order and
@@ -185,7 +189,12 @@ eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uint64_t n_edg
 
 /* eh_count -- COUNT(*) of `pattern` over the whole graph (subset == NULL or
  * subset_len == 0) or over the subgraph induced by `subset` (host array of
- * original ids, any order, repeats allowed).  Writes *out_count (host). */
+ * original ids, any order, repeats allowed).  Writes *out_count (host).
+ * The COUNT(*) queries of Table 1, evaluated by Algorithm 1 (Generic-Join)
+ * with the attribute order of the Sec. 3.3.2 loop nest on the pruned trie of
+ * App. A.1.2 (x > y > z: each triangle, each 4-clique once).  The induced
+ * subgraph restriction is not in the paper (a batching pattern of this
+ * library, see eh_count_batch). */
 eh_status eh_count(const eh_trie *trie, eh_pattern pattern, const uint32_t *subset, uint32_t subset_len,
                    void *stream, uint64_t *out_count);
 
@@ -205,6 +214,43 @@ eh_status eh_count_async(const eh_trie *trie, eh_pattern pattern, const eh_exec_
  * status word of the trie's last asynchronous counts (then clears it). */
 eh_status eh_count_status(const eh_trie *trie, void *stream);
 
+/* eh_count_range -- one part of a whole-graph count split across `nparts`
+ * workers, such as one process per GPU each holding a replica of the trie:
+ * the sum of the results of parts 0 .. nparts-1 is eh_count's result.  Not
+ * in the paper, which runs on one shared-memory node (Sec. 5.1.4); the parts
+ * split the outermost loop of Algorithm 1 (the vertex x of the Sec. 3.3.2
+ * loop nest), whose iterations are independent.
+ *   pattern     EH_TRIANGLE, EH_CLIQUE4, EH_LOLLIPOP or EH_LOLLIPOP_DISTINCT
+ *               (each a sum over the outer vertices); EH_BARBELL is EH_EINVAL
+ *   part        0 .. nparts-1; nparts >= 1 (else EH_EINVAL)
+ *   out_count   host uint64: this part's share.  The call synchronises `stream`.
+ * The work plan's heavy and light lists (heaviest first) are each cut into
+ * nparts contiguous ranges of about equal estimated cost (per vertex u,
+ * sum over v in N+(u) of |N+(v)|; as eh_range_bounds); the first call on a
+ * plan copies the lists' cost prefix sums to the host (8 bytes per listed
+ * vertex).  A trie with the block layout is counted here with the set-level
+ * kernel.  Serialised with the other synchronous counts of the trie. */
+eh_status eh_count_range(const eh_trie *trie, eh_pattern pattern, uint32_t part, uint32_t nparts,
+                         const eh_exec_opts *xopts, void *stream, uint64_t *out_count);
+
+/* eh_count_range_async -- as eh_count_range with the result written to device
+ * memory d_out_count (8 bytes, caller-owned) and no host synchronisation;
+ * the same ordering rules as eh_count_async (device errors come back through
+ * eh_count_status). */
+eh_status eh_count_range_async(const eh_trie *trie, eh_pattern pattern, uint32_t part, uint32_t nparts,
+                               const eh_exec_opts *xopts, void *stream, uint64_t *d_out_count);
+
+/* eh_range_bounds -- the split eh_count_range applies to each list, on host
+ * arrays (no device work): items 0 .. n-1 with costs cost[0 .. n-1] in list
+ * order; part `part` of `nparts` is the items [*lo, *hi), those whose cost
+ * prefix P(i) = cost[0] + ... + cost[i-1] has P(i) * nparts in
+ * [part * total, (part + 1) * total) (the last part also takes the items with
+ * P(i) = total).  Consecutive parts are adjacent and together cover 0 .. n-1
+ * once; each part's cost is within one item's cost of total / nparts.
+ * EH_EINVAL on a bad argument, EH_EOVERFLOW when the total exceeds uint64. */
+eh_status eh_range_bounds(const uint64_t *cost, uint64_t n, uint32_t part, uint32_t nparts, uint64_t *lo,
+                          uint64_t *hi);
+
 /* eh_count_noalloc -- a whole-graph count (as eh_count) that allocates
  * nothing.  For callers that may not allocate device memory while they
  * count: a process that has handed its device memory to a fixed pool or
@@ -213,11 +259,20 @@ eh_status eh_count_status(const eh_trie *trie, void *stream);
  *   trie       a trie built by eh_build_trie whose work plan exists: call
  *              eh_count_info_get (or any whole-graph count) on it once first,
  *              otherwise EH_EINVAL.
+ *   pattern    EH_TRIANGLE, EH_CLIQUE4, EH_LOLLIPOP or EH_LOLLIPOP_DISTINCT;
+ *              EH_BARBELL (which needs a per-vertex array) is EH_EINVAL.  A
+ *              trie with the block layout is counted with the set-level
+ *              kernel (same result as eh_count).
  *   out_count  host uint64, written on success.  The call synchronises `stream`.
  * Scratch (work counters, accumulators, status word and the 4-clique spill
  * arena) lives in one 32 MiB static device array that every device using the
- * library keeps until the process exits.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current.
+ * library keeps until the process exits.  The first eh_build_trie on a
+ * device makes it resident there: it looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current; this commits the array's
+ * memory) and runs the kernels this call launches once on empty work lists.
+ * On a device where no trie was built, the first call does that set-up
+ * itself (and may then allocate); make that first call before any stream
+ * capture.
  * The 4-clique pattern needs max out-degree x launch warps x 4 bytes of arena
  * when the max out-degree exceeds 512; above 32 MiB the call returns
  * EH_EINVAL with the sizes in eh_last_error, before launching anything.
@@ -227,20 +282,33 @@ eh_status eh_count_status(const eh_trie *trie, void *stream);
 eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, void *stream, uint64_t *out_count);
 
 /* eh_count_info_get -- work-plan facts of a whole-graph count (builds the
- * plan if needed): alg_bytes = the bytes the method must move in one pass
- * (staged sets once per vertex; per intersection the stored layout's bytes
- * of the other set, or 32 bytes per probe on the galloping side; 8 bytes per
- * edge of offsets), the number of heavy (CTA) and light (warp) vertices, and
- * the kernel launches one eh_count_async enqueues.  alg_bytes of the triangle
- * pass (also reported for the lollipop and barbell) is computed by a device
- * pass on the first call for a plan and cached; the call synchronises
- * `stream`.  For EH_CLIQUE4 alg_bytes is 0 (not computed). */
+ * plan if needed): the bytes the method must move in one pass (the
+ * set-intersection inner loop of Algorithm 1, where the paper finds up to
+ * 95% of Generic-Join's runtime, Sec. 1), the number of heavy (CTA) and light (warp)
+ * vertices, and the kernel launches one eh_count_async enqueues.
+ *   alg_bytes  a lower bound over the stored layouts (Sec. 4.1): the staged
+ *              set once per vertex in its cheaper form; per intersection the
+ *              cheapest way to read what of the other set can meet the
+ *              staged prefix (its uint array, the bitset words overlapping
+ *              the staged set's range, or at most 32 bytes per probe); 8
+ *              bytes per edge of offsets.  Triangle family (also the lollipop
+ *              and barbell): the pairs (N+(u)_<v, N+(v)).  EH_CLIQUE4: level 1
+ *              as the triangle, level 2 the pairs (S_<z, N+(z)) of every
+ *              S = N+(x) ∩ N+(y), plus 8 bytes per element of S when S is
+ *              longer than the kernel's 512-element on-chip buffer.
+ *   alg_bytes_stored  triangle family only (0 for EH_CLIQUE4): every set at
+ *              its stored layout's size (4|S| uint, 4 x words bitset), N+(u)
+ *              once per u, N+(v) once per pair unless |N+(v)| > 32 |N+(u)|,
+ *              then at most 32 bytes per element of N+(u); 8 bytes per edge.
+ * Each figure is computed by a device pass on the first call for a plan and
+ * cached; the call synchronises `stream`. */
 typedef struct {
     double alg_bytes;
     uint64_t n_heavy;
     uint64_t n_light;
     uint32_t kernel_launches;
     uint32_t reserved;
+    double alg_bytes_stored;
 } eh_count_info;
 
 eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts, void *stream,
@@ -310,7 +378,9 @@ eh_status eh_trim_memory(void);
 eh_status eh_trie_export_blocks(const eh_trie *trie, uint64_t *off, uint32_t *dir, uint32_t *words,
                                 uint64_t *n_blocks, uint64_t *n_bit_blocks);
 
-/* eh_count_batch -- n_queries independent queries in one persistent launch.
+/* eh_count_batch -- not in the paper (a batching pattern of this library;
+ * each query is one Table 1 COUNT(*) over an induced subgraph, evaluated as
+ * eh_count does).  n_queries independent queries in one persistent launch.
  * Each query's count goes to out_counts[i] and its status to out_status[i]
  * (a failing query does not fail the others; the call returns the first
  * non-OK status, or EH_OK).  subset_pool is a host array of pool_len ids. */
@@ -340,7 +410,14 @@ typedef struct {
 
 eh_status eh_batch_profile_get(eh_batch_profile *out);
 
-eh_status eh_trie_stats_get(const eh_trie *trie, eh_trie_stats *out);
+/* eh_trie_stats -- facts of a built trie (host struct, no device work):
+ * sizes, max degree and out-degree, how many pruned sets the layout rule of
+ * Sec. 4.4 made bitsets, device bytes held, and the density skew of the
+ * degree distribution as the paper measures it (Pearson's first skewness
+ * coefficient, Sec. 4 footnote).  EH_EINVAL on NULL. */
+eh_status eh_trie_stats(const eh_trie *trie, eh_trie_stats_t *out);
+/* the same call under its earlier name */
+eh_status eh_trie_stats_get(const eh_trie *trie, eh_trie_stats_t *out);
 
 /* eh_trie_export -- copies the trie to host arrays for inspection (tests).
  * Any output pointer may be NULL.  Sizes: new_to_old[n], out_off[n+1]
@@ -353,6 +430,9 @@ eh_status eh_trie_export(const eh_trie *trie, uint32_t which, uint32_t *new_to_o
                          uint32_t *out_len, uint32_t *out_nbr, uint32_t *bits_lo, uint32_t *bits_nwords,
                          uint64_t *bits_off, uint32_t *out_words);
 
+/* eh_free_trie -- no counterpart in the paper (resource release of this
+ * library).  Waits for the device, then releases every array of the trie
+ * (NULL is ignored).  Servers created on the trie must be destroyed first. */
 void eh_free_trie(eh_trie *trie);
 
 /* eh_test_fail_alloc_after -- failure injection for tests: the n-th device
@@ -369,6 +449,9 @@ void eh_test_fail_alloc_after(long long n);
  * the failure path; no GPU fault is involved. */
 eh_status eh_selftest_wait_timeout(uint32_t limit_us, void *stream);
 
+/* eh_last_error -- no counterpart in the paper (error reporting of this
+ * library): the calling thread's message of its last failed call, valid until
+ * the thread's next call; never NULL. */
 const char *eh_last_error(void);
 
 /* ---------------------------------------------------------------- serving

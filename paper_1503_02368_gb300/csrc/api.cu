@@ -10,9 +10,6 @@ thread_local char g_err[1024] = "";
 
 enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2 };
 
-// scratch layout (unsigned long long words of eh_trie::d_scratch)
-enum { SC_T = 0, SC_S = 1, SC_CNT = 2 /* 2 words */, SC_K4 = 4, SC_CNT2 = 6 /* 2 words */ };
-
 // result of a pattern from the accumulators: T (triangles), S (sum over
 // triangles of the three degrees), K (4-cliques)
 __global__ void k_finalize(const unsigned long long *acc, int pattern, unsigned long long *out, uint32_t *status) {
@@ -86,7 +83,7 @@ eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, 
     WorkPlan *plan = nullptr;
     EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
     unsigned long long *sc = t->d_scratch;
-    EH_CUDA_TRY(cudaMemsetAsync(sc, 0, 8 * sizeof(unsigned long long), s));
+    EH_CUDA_TRY(cudaMemsetAsync(sc, 0, SC_WORDS * sizeof(unsigned long long), s));
     if (pattern == EH_BARBELL) {
         // node 1 and 2 of the GHD: per-vertex triangle counts; root: the U(x,x') pass
         unsigned long long *vt = nullptr;
@@ -119,6 +116,13 @@ eh_status enqueue_count(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, 
 bool valid_pattern(int p) { return p >= EH_TRIANGLE && p <= EH_BARBELL; }
 
 }  // namespace
+
+eh_status eh_launch_finalize(const unsigned long long *acc, int pattern, unsigned long long *out, uint32_t *status,
+                             cudaStream_t s) {
+    k_finalize<<<1, 1, 0, s>>>(acc, pattern, out, status);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
+}
 
 eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
                            unsigned long long *d_out) {
@@ -219,6 +223,100 @@ extern "C" eh_status eh_count_status(const eh_trie *trie, void *stream) {
     return check_status(const_cast<eh_trie *>(trie), (cudaStream_t)stream);
 }
 
+// ------------------------------------------------------------- range counts
+//
+// One part of a whole-graph count: the plan's heavy and light lists are each
+// cut into `nparts` contiguous, cost-balanced ranges (eh_split_range over the
+// lists' cost prefixes) and the count kernel runs over this part's ranges
+// only.  The parts' results sum to the whole count.
+
+namespace {
+
+bool range_pattern(int p) { return p == EH_TRIANGLE || p == EH_CLIQUE4 || p == EH_LOLLIPOP || p == EH_LOLLIPOP_DISTINCT; }
+
+eh_status enqueue_range(eh_trie *t, eh_pattern pattern, uint32_t part, uint32_t nparts, const eh_exec_opts &xo,
+                        cudaStream_t s, unsigned long long *d_out) {
+    NvtxRange nv("eh_count_range");
+    WorkPlan *plan = nullptr;
+    EH_TRY(eh_plan_get(t, xo.light_max, s, &plan));
+    EH_TRY(eh_plan_cost_prefix(t, plan, s));
+    uint64_t hlo, hhi, llo, lhi;
+    eh_split_range(plan->h_heavy_pre.data(), plan->n_heavy, part, nparts, &hlo, &hhi);
+    eh_split_range(plan->h_light_pre.data(), plan->n_light, part, nparts, &llo, &lhi);
+    WorkPlan sub;   // the part's ranges of the lists (no ownership)
+    sub.light_max = plan->light_max;
+    sub.d_heavy = plan->d_heavy + hlo;
+    sub.n_heavy = (uint32_t)(hhi - hlo);
+    sub.d_light = plan->d_light + llo;
+    sub.n_light = (uint32_t)(lhi - llo);
+    unsigned long long *sc = t->d_scratch;
+    EH_CUDA_TRY(cudaMemsetAsync(sc, 0, SC_WORDS * sizeof(unsigned long long), s));
+    if (pattern == EH_CLIQUE4) {
+        EH_TRY(eh_launch_clique4(t, sub, t->view(), xo, s, sc + SC_K4, sc + SC_CNT2, t->d_status, nullptr, 0));
+    } else {
+        // set-level kernel also on a block-layout trie (its uint arrays and bitsets are kept)
+        const int mode = pattern == EH_TRIANGLE ? M_COUNT : M_LOLLI;
+        EH_TRY(eh_launch_triangle(t, sub, t->view(), mode, xo, s, sc + SC_T, sc + SC_CNT, t->d_status, nullptr,
+                                  nullptr));
+    }
+    k_finalize<<<1, 1, 0, s>>>(sc, (int)pattern, d_out, t->d_status);
+    EH_CUDA_TRY(cudaGetLastError());
+    return EH_OK;
+}
+
+eh_status check_range_args(const eh_trie *trie, int pattern, uint32_t part, uint32_t nparts, const char *who) {
+    if (!trie) { eh_set_error("%s: NULL trie", who); return EH_EINVAL; }
+    if (!range_pattern(pattern)) {
+        eh_set_error("%s: pattern %d cannot be split (triangle, 4-clique and the lollipops only)", who, pattern);
+        return EH_EINVAL;
+    }
+    if (nparts == 0 || part >= nparts) { eh_set_error("%s: part %u of %u parts", who, part, nparts); return EH_EINVAL; }
+    return EH_OK;
+}
+
+}  // namespace
+
+extern "C" eh_status eh_count_range(const eh_trie *trie, eh_pattern pattern, uint32_t part, uint32_t nparts,
+                                    const eh_exec_opts *xopts, void *stream, uint64_t *out_count) {
+    EH_TRY(check_range_args(trie, pattern, part, nparts, "eh_count_range"));
+    if (!out_count) { eh_set_error("eh_count_range: NULL out_count"); return EH_EINVAL; }
+    eh_trie *t = const_cast<eh_trie *>(trie);
+    cudaStream_t s = (cudaStream_t)stream;
+    const eh_exec_opts xo = eh_exec_defaults(xopts);
+    std::lock_guard<std::mutex> g(t->call_mu);
+    unsigned long long *d_out = t->d_scratch + 15;
+    EH_TRY(enqueue_range(t, pattern, part, nparts, xo, s, d_out));
+    unsigned long long r = 0;
+    EH_CUDA_TRY(cudaMemcpyAsync(&r, d_out, 8, cudaMemcpyDeviceToHost, s));
+    EH_TRY(check_status(t, s));
+    *out_count = r;
+    return EH_OK;
+}
+
+extern "C" eh_status eh_count_range_async(const eh_trie *trie, eh_pattern pattern, uint32_t part, uint32_t nparts,
+                                          const eh_exec_opts *xopts, void *stream, uint64_t *d_out_count) {
+    EH_TRY(check_range_args(trie, pattern, part, nparts, "eh_count_range_async"));
+    if (!d_out_count) { eh_set_error("eh_count_range_async: NULL d_out_count"); return EH_EINVAL; }
+    const eh_exec_opts xo = eh_exec_defaults(xopts);
+    return enqueue_range(const_cast<eh_trie *>(trie), pattern, part, nparts, xo, (cudaStream_t)stream,
+                         (unsigned long long *)d_out_count);
+}
+
+extern "C" eh_status eh_range_bounds(const uint64_t *cost, uint64_t n, uint32_t part, uint32_t nparts, uint64_t *lo,
+                                     uint64_t *hi) {
+    if ((n && !cost) || !lo || !hi || nparts == 0 || part >= nparts) {
+        eh_set_error("eh_range_bounds: bad argument");
+        return EH_EINVAL;
+    }
+    std::vector<uint64_t> pre((size_t)n + 1, 0);
+    for (uint64_t i = 0; i < n; ++i) {
+        if (pre[i] + cost[i] < pre[i]) { eh_set_error("eh_range_bounds: total cost exceeds uint64"); return EH_EOVERFLOW; }
+        pre[i + 1] = pre[i] + cost[i];
+    }
+    eh_split_range(pre.data(), n, part, nparts, lo, hi);
+    return EH_OK;
+}
+
 extern "C" eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, const eh_exec_opts *xopts,
                                        void *stream, eh_count_info *out) {
     if (!trie || !out) { eh_set_error("eh_count_info_get: NULL argument"); return EH_EINVAL; }
@@ -227,10 +325,16 @@ extern "C" eh_status eh_count_info_get(const eh_trie *trie, eh_pattern pattern, 
     eh_exec_opts xo = eh_exec_defaults(xopts);
     WorkPlan *plan = nullptr;
     EH_TRY(eh_plan_get(t, xo.light_max, (cudaStream_t)stream, &plan));
-    double alg = 0;
-    if (pattern != EH_CLIQUE4) EH_TRY(eh_plan_alg_bytes(t, plan, (cudaStream_t)stream, &alg));
+    double alg = 0, stored = 0;
+    if (pattern == EH_CLIQUE4) {
+        EH_TRY(eh_plan_alg_bytes(t, plan, (cudaStream_t)stream, ALG_K4, &alg));
+    } else {
+        EH_TRY(eh_plan_alg_bytes(t, plan, (cudaStream_t)stream, ALG_TRI, &alg));
+        EH_TRY(eh_plan_alg_bytes(t, plan, (cudaStream_t)stream, ALG_TRI_STORED, &stored));
+    }
     memset(out, 0, sizeof(*out));
-    out->alg_bytes = pattern == EH_CLIQUE4 ? plan->alg_bytes_k4 : alg;
+    out->alg_bytes = alg;
+    out->alg_bytes_stored = stored;
     out->n_heavy = plan->n_heavy;
     out->n_light = plan->n_light;
     out->kernel_launches = 2;   // the count kernel and the finalize kernel
@@ -250,7 +354,7 @@ extern "C" eh_status eh_vertex_triangles(const eh_trie *trie, void *stream, uint
     eh_status st = dev_alloc(&vo, t->n, s);
     if (st == EH_OK) {
         cudaMemsetAsync(vt, 0, (uint64_t)t->n * 8, s);
-        cudaMemsetAsync(t->d_scratch, 0, 8 * sizeof(unsigned long long), s);
+        cudaMemsetAsync(t->d_scratch, 0, SC_WORDS * sizeof(unsigned long long), s);
         st = eh_launch_triangle(t, *plan, t->view(), M_VERTEX, xo, s, t->d_scratch + SC_T, t->d_scratch + SC_CNT,
                                 t->d_status, vt, nullptr);
     }
@@ -296,7 +400,7 @@ extern "C" eh_status eh_count_selected(const eh_trie *trie, eh_sel_pattern patte
     EH_TRY(dev_alloc(&vt, (uint64_t)t->n + 1, s));
     eh_status st = EH_OK;
     if (cudaMemsetAsync(vt, 0, ((uint64_t)t->n + 1) * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(t->d_scratch, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess)
+        cudaMemsetAsync(t->d_scratch, 0, SC_WORDS * sizeof(unsigned long long), s) != cudaSuccess)
         st = EH_ECUDA;
     if (st == EH_OK)
         st = eh_launch_triangle(t, *plan, t->view(), M_VERTEX, xo, s, t->d_scratch + SC_T, t->d_scratch + SC_CNT,

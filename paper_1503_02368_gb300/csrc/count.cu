@@ -1084,15 +1084,23 @@ eh_status eh_launch_batch(const BatchView &bv, const uint32_t *heavy, uint32_t n
 namespace {
 
 constexpr uint64_t NOALLOC_WORDS = 8ull << 20;   // 32 MiB of 32-bit words
-constexpr uint64_t NOALLOC_HEAD = 64;            // counters, accumulators, status; arena after
+constexpr uint64_t NOALLOC_HEAD = 64;            // 32-bit words before the arena
+// in the head: the SC_* accumulators and counters (unsigned long long words
+// 0 .. SC_WORDS-1), the result, the status word
+constexpr uint64_t NOALLOC_RESULT = SC_WORDS;            // unsigned long long word
+constexpr uint64_t NOALLOC_STATUS = 2 * (SC_WORDS + 1);  // 32-bit word
+static_assert(NOALLOC_STATUS < NOALLOC_HEAD, "scratch head too small");
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[256] = {};
 
 // Device address of the array on the current device, looked up once per
-// device (the name is only a host-side stand-in for it).
-eh_status noalloc_scratch(uint32_t **out) {
+// device (the name is only a host-side stand-in for it).  The lookup loads
+// this file's module, which commits the array's memory.  The kernels the call
+// launches are then run once on empty work lists (no item is read), so that
+// whatever their first launch sets up is in place before the first call.
+eh_status noalloc_scratch(uint32_t **out, cudaStream_t s) {
     int dev = 0;
     EH_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) { eh_set_error("eh_count_noalloc: device ordinal %d out of range", dev); return EH_EINVAL; }
@@ -1104,34 +1112,39 @@ eh_status noalloc_scratch(uint32_t **out) {
             eh_set_error("eh_count_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
             return EH_ECUDA;
         }
+        uint32_t *scr = (uint32_t *)p;
+        unsigned long long *sc = (unsigned long long *)scr;
+        const int smem4 = (BM_CAP_WORDS + 8 * (S_CAP + SB_CAP_WORDS)) * 4;
+        EH_CUDA_TRY(cudaFuncSetAttribute(k_clique4<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4));
+        TrieView none{};
+        EH_CUDA_TRY(cudaMemsetAsync(scr, 0, NOALLOC_HEAD * 4, s));
+        k_triangle<M_COUNT, 8><<<1, 8 * 32, BM_CAP_WORDS * 4, s>>>(none, nullptr, 0, nullptr, 0, 32, sc + SC_CNT,
+                                                                    sc + SC_T, scr + NOALLOC_STATUS, nullptr);
+        k_triangle<M_LOLLI, 8><<<1, 8 * 32, BM_CAP_WORDS * 4, s>>>(none, nullptr, 0, nullptr, 0, 32, sc + SC_CNT,
+                                                                    sc + SC_T, scr + NOALLOC_STATUS, nullptr);
+        k_clique4<8><<<1, 8 * 32, smem4, s>>>(none, nullptr, 0, nullptr, 0, 32, sc + SC_CNT2, sc + SC_K4,
+                                              scr + NOALLOC_STATUS, nullptr, 0);
+        EH_CUDA_TRY(cudaGetLastError());
+        EH_TRY(eh_launch_finalize(sc, EH_TRIANGLE, sc + NOALLOC_RESULT, scr + NOALLOC_STATUS, s));
+        EH_CUDA_TRY(cudaStreamSynchronize(s));
         g_noalloc_addr[dev] = p;
     }
     *out = (uint32_t *)g_noalloc_addr[dev];
     return EH_OK;
 }
 
-__global__ void k_noalloc_finalize(const unsigned long long *acc, int pattern, unsigned long long *out,
-                                   uint32_t *status) {
-    const unsigned long long T = acc[0], S = acc[1], K = acc[2];
-    unsigned long long r = 0;
-    switch (pattern) {
-        case EH_TRIANGLE: r = T; break;
-        case EH_CLIQUE4: r = K; break;
-        case EH_LOLLIPOP:
-            if (S >> 63) atomicOr(status, DEV_ST_OVERFLOW);
-            r = 2ull * S;
-            break;
-        default: r = S - 6ull * T; break;
-    }
-    *out = r;
-}
-
 }  // namespace
+
+eh_status eh_noalloc_setup(cudaStream_t s) {
+    uint32_t *p = nullptr;
+    return noalloc_scratch(&p, s);
+}
 
 extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, void *stream, uint64_t *out_count) {
     if (!trie || !out_count) { eh_set_error("eh_count_noalloc: NULL argument"); return EH_EINVAL; }
     if (pattern < EH_TRIANGLE || pattern > EH_LOLLIPOP_DISTINCT) {
-        eh_set_error("eh_count_noalloc: unknown pattern %d", (int)pattern);
+        eh_set_error("eh_count_noalloc: pattern %d not supported (triangle, 4-clique and the lollipops only)",
+                     (int)pattern);
         return EH_EINVAL;
     }
     eh_trie *t = const_cast<eh_trie *>(trie);
@@ -1147,13 +1160,12 @@ extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, v
                      "whole-graph count) on it once first");
         return EH_EINVAL;
     }
-    uint32_t *scr = nullptr;
-    EH_TRY(noalloc_scratch(&scr));
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long *counters = (unsigned long long *)scr;       // words 0..3
-    unsigned long long *acc = (unsigned long long *)(scr + 4);      // words 4..9: T, S, K
-    unsigned long long *res = (unsigned long long *)(scr + 10);     // words 10..11: the count
-    uint32_t *status = scr + 12;
+    uint32_t *scr = nullptr;
+    EH_TRY(noalloc_scratch(&scr, s));
+    unsigned long long *sc = (unsigned long long *)scr;               // SC_* layout
+    unsigned long long *res = sc + NOALLOC_RESULT;
+    uint32_t *status = scr + NOALLOC_STATUS;
     uint32_t *arena = scr + NOALLOC_HEAD;
     const uint64_t arena_cap = NOALLOC_WORDS - NOALLOC_HEAD;
     const TrieView tv = t->view();
@@ -1183,7 +1195,7 @@ extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, v
     EH_CUDA_TRY(cudaMemsetAsync(scr, 0, NOALLOC_HEAD * 4, s));
     if (pattern == EH_CLIQUE4) {
         kern4<<<grid4, 8 * 32, smem4, s>>>(tv, plan->d_heavy, plan->n_heavy, plan->d_light, plan->n_light,
-                                           xo.gallop_ratio, counters, acc + 2, status,
+                                           xo.gallop_ratio, sc + SC_CNT2, sc + SC_K4, status,
                                            per_warp ? arena : nullptr, per_warp);
     } else {
         auto kern = pattern == EH_TRIANGLE ? k_triangle<M_COUNT, 8> : k_triangle<M_LOLLI, 8>;
@@ -1192,10 +1204,10 @@ extern "C" eh_status eh_count_noalloc(const eh_trie *trie, eh_pattern pattern, v
         EH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 8 * 32, smem));
         unsigned grid = (unsigned)(eh_num_sms() * (per_sm < 1 ? 1 : per_sm));
         kern<<<grid, 8 * 32, smem, s>>>(tv, plan->d_heavy, plan->n_heavy, plan->d_light, plan->n_light,
-                                        xo.gallop_ratio, counters, acc, status, nullptr);
+                                        xo.gallop_ratio, sc + SC_CNT, sc + SC_T, status, nullptr);
     }
-    k_noalloc_finalize<<<1, 1, 0, s>>>(acc, (int)pattern, res, status);
     EH_CUDA_TRY(cudaGetLastError());
+    EH_TRY(eh_launch_finalize(sc, (int)pattern, res, status, s));
     unsigned long long r = 0;
     uint32_t st = 0;
     EH_CUDA_TRY(cudaMemcpyAsync(&r, res, 8, cudaMemcpyDeviceToHost, s));

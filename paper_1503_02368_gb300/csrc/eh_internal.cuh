@@ -47,6 +47,18 @@ enum : uint32_t {
     DEV_ST_RANGE = 8u,     // a listing row fell outside the range its count pass gave it (not written)
 };
 
+// Scratch layout of a whole-graph count (unsigned long long words of
+// eh_trie::d_scratch, and of the static array of eh_count_noalloc): the
+// accumulators the count kernels add into and their work counters.
+enum {
+    SC_T = 0,      // triangles
+    SC_S = 1,      // sum over triangles of the three degrees (lollipop)
+    SC_CNT = 2,    // 2 words: next heavy item, next light chunk (triangle kernels)
+    SC_K4 = 4,     // 4-cliques (also the barbell's sum)
+    SC_CNT2 = 6,   // 2 words: the 4-clique kernel's work counters
+    SC_WORDS = 8   // words cleared before each count
+};
+
 // ------------------------------------------------------------ set layouts
 //
 // Every pruned set N+(v) is kept as a sorted uint32 array in `nbr`, starting
@@ -96,8 +108,14 @@ struct WorkPlan {
     uint32_t n_light = 0;
     uint32_t *d_heavy_blk = nullptr;   // block layout only: the heavy list, big items first (blocks.cu)
     uint32_t n_big = 0;
-    double alg_bytes = 0;          // algorithmic bytes of one triangle pass (< 0: not computed yet)
-    double alg_bytes_k4 = 0;       // algorithmic bytes of one 4-clique pass
+    // algorithmic bytes of one pass (< 0: not computed yet; eh_plan_alg_bytes)
+    double alg_bytes = -1.0;        // triangle pass, lower bound over the stored layouts
+    double alg_bytes_stored = -1.0; // triangle pass, each set at its stored layout's size
+    double alg_bytes_k4 = -1.0;     // 4-clique pass, lower bound (both levels, spills)
+    uint64_t *d_cost = nullptr;     // per vertex: sum_{v in N+(u)} |N+(v)| (the lists' order key)
+    // exclusive prefix sums of d_cost along the heavy and the light list
+    // (n_heavy + 1 and n_light + 1 entries), built on the first range count
+    std::vector<uint64_t> h_heavy_pre, h_light_pre;
 };
 
 struct eh_trie {
@@ -206,8 +224,17 @@ int eh_num_sms();
 
 // Count entry points shared between files.
 eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan **out);
-// the plan's algorithmic bytes of one triangle pass, computed on first use
-eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, double *out);
+// a plan's algorithmic bytes of one pass, computed on first use and cached:
+// which = ALG_TRI (lower bound), ALG_TRI_STORED (stored layouts), ALG_K4
+enum { ALG_TRI = 0, ALG_TRI_STORED = 1, ALG_K4 = 2 };
+eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, int which, double *out);
+// the cost prefixes of the plan's lists on the host (built on first use)
+eh_status eh_plan_cost_prefix(eh_trie *t, WorkPlan *p, cudaStream_t s);
+// part `part` of `nparts` contiguous ranges of a list whose items have the
+// exclusive cost prefix pre[0..n]: [*lo, *hi), the items i with
+// pre[i] * nparts in [part * total, (part + 1) * total) -- every item in
+// exactly one part, each part within one item's cost of total / nparts
+void eh_split_range(const uint64_t *pre, uint64_t n, uint32_t part, uint32_t nparts, uint64_t *lo, uint64_t *hi);
 // eh_launch_triangle modes: 0 count, 1 lollipop, 2 per-vertex t (d_vt[n]),
 // TRI_MODE_APEX: each work item's triangles in which it is the largest id, to
 // d_vt[item] for heavy items and d_vt[n_heavy + i] for light item i
@@ -250,6 +277,14 @@ eh_status eh_launch_tri_blocks(eh_trie *t, const WorkPlan &plan, cudaStream_t s,
 eh_status eh_host_out_degrees(eh_trie *t);
 // SK4 per-x sum over the selected vertex's neighbours (list.cu)
 eh_status eh_sk4_total(eh_trie *t, uint32_t node_new, const eh_exec_opts &xo, cudaStream_t s, uint64_t *total);
+// the result of `pattern` from the SC_* accumulators at acc, to *out (api.cu)
+eh_status eh_launch_finalize(const unsigned long long *acc, int pattern, unsigned long long *out, uint32_t *status,
+                             cudaStream_t s);
+// eh_count_noalloc's set-up on the current device (count.cu), once per
+// device: resolves the static scratch array's device address and runs the
+// kernels the call launches once on empty work lists (on `s`, synchronised),
+// so that the array and the kernels are resident before the first call
+eh_status eh_noalloc_setup(cudaStream_t s);
 eh_status eh_enqueue_whole(eh_trie *t, eh_pattern pattern, const eh_exec_opts &xo, cudaStream_t s,
                            unsigned long long *d_out);
 eh_status eh_check_status(eh_trie *t, cudaStream_t s);

@@ -63,6 +63,116 @@ __global__ void k_alg_bytes(TrieView tv, uint32_t n, uint32_t ratio, unsigned lo
     if (lane == 0 && b) atomicAdd(bytes_acc, (unsigned long long)b);
 }
 
+// one warp per vertex: the same pass counted with every set at its stored
+// layout's size -- bytes(X) = 4|X| for a uint set, 4 x its words for a bitset
+// set -- and the pair (u, v) read as N+(u) ∩ N+(v) in full: u's set once,
+// then per v in N+(u) the bytes of N+(v), or at most 32 bytes per element of
+// N+(u) when |N+(v)| > ratio |N+(u)| (the galloping side).  Reported next to
+// the lower bound above.
+__global__ void k_alg_bytes_stored(TrieView tv, uint32_t n, uint32_t ratio, unsigned long long *bytes_acc) {
+    const uint32_t u = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= n) return;
+    const SetDesc du = tv.desc[u];
+    uint64_t b = 0;
+    for (uint32_t j = lane; j < du.len; j += 32) {
+        const SetDesc dv = tv.desc[tv.nbr[du.off + j]];
+        uint64_t bb = dv.nwords ? 4ull * dv.nwords : 4ull * dv.len;
+        if ((uint64_t)dv.len > (uint64_t)ratio * du.len && 32ull * du.len < bb) bb = 32ull * du.len;
+        b += bb;
+    }
+    if (lane == 0) b += du.nwords ? 4ull * du.nwords : 4ull * du.len;
+    for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
+    if (lane == 0 && b) atomicAdd(bytes_acc, (unsigned long long)b);
+}
+
+// the per-warp shared buffer of S in the 4-clique kernels (K4_S_CAP): a
+// longer S is written to and read back from device memory
+constexpr uint32_t K4_SPILL_FROM = K4_S_CAP;
+
+// bytes of the pair (P, N+(z)) with P a set held on chip: r elements, words
+// [p_lo, p_hi) of the value domain; the lower-bound reading of k_alg_bytes
+__device__ __forceinline__ uint64_t pair_bytes(const SetDesc &dz, uint32_t r, uint32_t p_lo, uint32_t p_hi,
+                                               uint32_t ratio) {
+    uint64_t bb = 4ull * dz.len;
+    if ((uint64_t)dz.len > (uint64_t)ratio * r && 32ull * r < bb) bb = 32ull * r;
+    if (dz.nwords) {
+        const uint32_t lo = p_lo > dz.lo_word ? p_lo : dz.lo_word;
+        const uint32_t hi = p_hi < dz.lo_word + dz.nwords ? p_hi : dz.lo_word + dz.nwords;
+        uint64_t wb = hi > lo ? 4ull * (hi - lo) : 0ull;
+        if (32ull * r < wb) wb = 32ull * r;
+        if (wb < bb) bb = wb;
+    }
+    return bb;
+}
+
+// one CTA per x: the bytes one 4-clique pass must move (Table 1's 4Clique,
+// x > y > z > w).  A = N+(x) once, in its cheaper stored form; level 1 per
+// (x, y = A[j]), j >= 2, |N+(y)| >= 2: the pair (A_<y, N+(y)) as in
+// k_alg_bytes; level 2 per z = S[r], r >= 1, of S = A ∩ N+(y): the pair
+// (S_<z, N+(z)), S_<z held on chip (r elements, words from S[0]'s down to
+// S[r-1]'s); plus 8 bytes per element of S (written and read back) when S is
+// longer than the on-chip buffer.  S is found by scanning N+(y) in rounds of
+// 32 with a binary search of each element in A.
+__global__ void k_alg_bytes_k4(TrieView tv, uint32_t n, uint32_t ratio, unsigned long long *bytes_acc) {
+    const uint32_t x = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (x >= n) return;
+    const SetDesc dx = tv.desc[x];
+    if (dx.len < 3) return;
+    const uint32_t *A = tv.nbr + dx.off;
+    const uint32_t a_lo = (A[0] >> 7) << 2, a_hi = (A[dx.len - 1] >> 5) + 1;
+    uint64_t b = 0;
+    if (threadIdx.x == 0) b += dx.nwords && dx.nwords < dx.len ? 4ull * dx.nwords : 4ull * dx.len;
+    for (uint32_t j = 2 + warp; j < dx.len; j += nwarps) {
+        const SetDesc dy = tv.desc[A[j]];
+        if (dy.len < 2) continue;
+        if (lane == 0) b += pair_bytes(dy, j, a_lo, a_hi, ratio);
+        const uint32_t *B = tv.nbr + dy.off;
+        uint32_t ns = 0, s0 = 0, prev = 0;
+        for (uint32_t c = 0; c < dy.len; c += 32) {
+            const uint32_t i = c + lane;
+            const uint32_t e = i < dy.len ? B[i] : 0u;
+            bool hit = false;
+            if (i < dy.len) {
+                uint32_t lo = 0, hi = j;   // e < A[j]: only A_<y can hold it
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (A[mid] < e) lo = mid + 1; else hi = mid;
+                }
+                hit = lo < j && A[lo] == e;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, hit);
+            if (!m) continue;
+            if (ns == 0) s0 = __shfl_sync(0xffffffffu, e, __ffs(m) - 1);
+            const uint32_t below = m & ((1u << lane) - 1u);
+            // the element before this lane's in S: a lower lane's, or the last of earlier rounds
+            const uint32_t pl = below ? 31u - __clz(below) : 0u;
+            const uint32_t pe = __shfl_sync(0xffffffffu, e, pl);
+            if (hit) {
+                const uint32_t r = ns + __popc(below);
+                const uint32_t before = below ? pe : prev;
+                if (r >= 1) {
+                    const SetDesc dz = tv.desc[e];
+                    if (dz.len) b += pair_bytes(dz, r, (s0 >> 7) << 2, (before >> 5) + 1, ratio);
+                }
+            }
+            ns += __popc(m);
+            prev = __shfl_sync(0xffffffffu, e, 31 - __clz(m));
+        }
+        if (lane == 0 && ns > K4_SPILL_FROM) b += 8ull * ns;
+    }
+    for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
+    if (lane == 0 && b) atomicAdd(bytes_acc, (unsigned long long)b);
+}
+
+// cost of the items of a list, in list order
+__global__ void k_gather_cost(const uint32_t *__restrict__ ids, uint32_t cnt, const uint64_t *__restrict__ cost,
+                              uint64_t *out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) out[i] = cost[ids[i]];
+}
+
 // class 0: heavy (len > light_max), 1: light (2 <= len <= light_max)
 __global__ void k_class_flags(TrieView tv, uint32_t n, uint32_t light_max, int cls, uint32_t *flags) {
     uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,28 +268,34 @@ eh_status eh_plan_get(eh_trie *t, uint32_t light_max, cudaStream_t s, WorkPlan *
         eh_set_error("plan: %s", cudaGetErrorString(cudaGetLastError()));
         st = EH_ECUDA;
     }
-    dev_free(cost, s);
     dev_free(olen, s);
     if (st != EH_OK) {
+        dev_free(cost, s);
         cudaFree(p.d_heavy);
         cudaFree(p.d_light);
         cudaFree(p.d_heavy_blk);
         return st;
     }
-    p.alg_bytes = -1.0;   // computed on the first request (eh_plan_alg_bytes)
+    p.d_cost = cost;      // kept: the range counts split the lists by it
     auto res = t->plans.emplace(light_max, p);
     *out = &res.first->second;
     return EH_OK;
 }
 
-eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, double *out) {
+eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, int which, double *out) {
     std::lock_guard<std::mutex> g(t->mu);
-    if (p->alg_bytes < 0) {
+    double *slot = which == ALG_K4 ? &p->alg_bytes_k4 : which == ALG_TRI_STORED ? &p->alg_bytes_stored : &p->alg_bytes;
+    if (*slot < 0) {
         unsigned long long *bytes_d = nullptr, bytes_h = 0;
         EH_TRY(dev_alloc(&bytes_d, 1, s));
         eh_status st = EH_OK;
         if (cudaMemsetAsync(bytes_d, 0, 8, s) != cudaSuccess) st = EH_ECUDA;
-        if (st == EH_OK && t->n) k_alg_bytes<<<(t->n + 7) / 8, 256, 0, s>>>(t->view(), t->n, 32, bytes_d);
+        if (st == EH_OK && t->n) {
+            if (which == ALG_K4) k_alg_bytes_k4<<<t->n, 256, 0, s>>>(t->view(), t->n, 32, bytes_d);
+            else if (which == ALG_TRI_STORED)
+                k_alg_bytes_stored<<<(t->n + 7) / 8, 256, 0, s>>>(t->view(), t->n, 32, bytes_d);
+            else k_alg_bytes<<<(t->n + 7) / 8, 256, 0, s>>>(t->view(), t->n, 32, bytes_d);
+        }
         if (st == EH_OK && (cudaMemcpyAsync(&bytes_h, bytes_d, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                             cudaStreamSynchronize(s) != cudaSuccess)) {
             eh_set_error("algorithmic bytes: %s", cudaGetErrorString(cudaGetLastError()));
@@ -187,8 +303,55 @@ eh_status eh_plan_alg_bytes(eh_trie *t, WorkPlan *p, cudaStream_t s, double *out
         }
         dev_free(bytes_d, s);
         EH_TRY(st);
-        p->alg_bytes = (double)bytes_h + 8.0 * (double)t->m;
+        *slot = (double)bytes_h + 8.0 * (double)t->m;
     }
-    *out = p->alg_bytes;
+    *out = *slot;
+    return EH_OK;
+}
+
+void eh_split_range(const uint64_t *pre, uint64_t n, uint32_t part, uint32_t nparts, uint64_t *lo, uint64_t *hi) {
+    // b(q) = the first i in [0, n] with pre[i] * nparts >= q * total; b(nparts) = n
+    const unsigned __int128 total = pre[n];
+    auto bound = [&](uint32_t q) -> uint64_t {
+        if (q == 0) return 0;
+        if (q >= nparts) return n;
+        const unsigned __int128 target = total * q;
+        uint64_t a = 0, b = n;
+        while (a < b) {
+            const uint64_t mid = a + (b - a) / 2;
+            if ((unsigned __int128)pre[mid] * nparts >= target) b = mid; else a = mid + 1;
+        }
+        return a;
+    };
+    *lo = bound(part);
+    *hi = bound(part + 1);
+}
+
+eh_status eh_plan_cost_prefix(eh_trie *t, WorkPlan *p, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(t->mu);
+    if (p->h_heavy_pre.size() == (size_t)p->n_heavy + 1 && p->h_light_pre.size() == (size_t)p->n_light + 1)
+        return EH_OK;
+    const uint32_t cnt = p->n_heavy > p->n_light ? p->n_heavy : p->n_light;
+    uint64_t *d = nullptr;
+    EH_TRY(dev_alloc(&d, cnt, s));
+    std::vector<uint64_t> hc[2];
+    const uint32_t *ids[2] = {p->d_heavy, p->d_light};
+    const uint32_t ns[2] = {p->n_heavy, p->n_light};
+    eh_status st = EH_OK;
+    for (int k = 0; k < 2 && st == EH_OK; ++k) {
+        hc[k].assign((size_t)ns[k] + 1, 0);
+        if (!ns[k]) continue;
+        k_gather_cost<<<(ns[k] + 255) / 256, 256, 0, s>>>(ids[k], ns[k], p->d_cost, d);
+        if (cudaMemcpyAsync(hc[k].data() + 1, d, (uint64_t)ns[k] * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            eh_set_error("range split: %s", cudaGetErrorString(cudaGetLastError()));
+            st = EH_ECUDA;
+        }
+        for (uint32_t i = 1; i <= ns[k]; ++i) hc[k][i] += hc[k][i - 1];   // exclusive prefix at i
+    }
+    dev_free(d, s);
+    EH_TRY(st);
+    p->h_heavy_pre.swap(hc[0]);
+    p->h_light_pre.swap(hc[1]);
     return EH_OK;
 }

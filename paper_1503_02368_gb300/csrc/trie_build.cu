@@ -254,6 +254,7 @@ void free_trie_arrays(eh_trie *t) {
         cudaFree(kv.second.d_heavy);
         cudaFree(kv.second.d_light);
         cudaFree(kv.second.d_heavy_blk);
+        if (kv.second.d_cost) cudaFreeAsync(kv.second.d_cost, 0);
     }
     t->plans.clear();
 }
@@ -616,6 +617,9 @@ extern "C" eh_status eh_build_trie(const uint32_t *src, const uint32_t *dst, uin
     t->n = n_vertices;
     t->opts = o;
     eh_status st = build(src, dst, n_edges, n_vertices, o, s, t);
+    // eh_count_noalloc's static scratch and kernels made resident on this
+    // device now, so that its calls load (and allocate) nothing
+    if (st == EH_OK) st = eh_noalloc_setup(s);
     if (st != EH_OK) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
@@ -634,7 +638,7 @@ extern "C" void eh_free_trie(eh_trie *t) {
     delete t;
 }
 
-extern "C" eh_status eh_trie_stats_get(const eh_trie *t, eh_trie_stats *o) {
+extern "C" eh_status eh_trie_stats_get(const eh_trie *t, eh_trie_stats_t *o) {
     if (!t || !o) { eh_set_error("eh_trie_stats_get: NULL argument"); return EH_EINVAL; }
     memset(o, 0, sizeof(*o));
     o->n_vertices = t->n;
@@ -650,6 +654,8 @@ extern "C" eh_status eh_trie_stats_get(const eh_trie *t, eh_trie_stats *o) {
     o->bitset_tau = t->opts.bitset_tau;
     return EH_OK;
 }
+
+extern "C" eh_status eh_trie_stats(const eh_trie *t, eh_trie_stats_t *o) { return eh_trie_stats_get(t, o); }
 
 extern "C" eh_status eh_trie_export(const eh_trie *t, uint32_t which, uint32_t *new_to_old, uint64_t *out_off,
                                     uint32_t *out_len, uint32_t *out_nbr, uint32_t *bits_lo, uint32_t *bits_nwords,

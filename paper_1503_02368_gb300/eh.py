@@ -49,7 +49,8 @@ class TrieStats(ctypes.Structure):
 
 class CountInfo(ctypes.Structure):
     _fields_ = [("alg_bytes", ctypes.c_double), ("n_heavy", ctypes.c_uint64), ("n_light", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("kernel_launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("alg_bytes_stored", ctypes.c_double)]
 
 
 class Query(ctypes.Structure):
@@ -69,7 +70,9 @@ class ServerStats(ctypes.Structure):
 
 
 EXPORTED = ["eh_build_trie", "eh_count", "eh_count_ex", "eh_count_noalloc", "eh_count_async", "eh_count_status", "eh_count_info_get",
-            "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_batch_profile_get", "eh_trie_stats_get", "eh_trie_export",
+            "eh_count_range", "eh_count_range_async", "eh_range_bounds",
+            "eh_vertex_triangles", "eh_count_batch", "eh_count_batch_ex", "eh_batch_profile_get", "eh_trie_stats",
+            "eh_trie_stats_get", "eh_trie_export",
             "eh_free_trie", "eh_last_error", "eh_selftest_wait_timeout", "eh_test_fail_alloc_after", "eh_server_create", "eh_server_submit", "eh_server_poll",
             "eh_server_wait", "eh_server_latency", "eh_server_stats_get", "eh_server_destroy"]
 
@@ -103,6 +106,14 @@ def lib():
     L.eh_count_async.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, vp]
     L.eh_count_status.restype = st
     L.eh_count_status.argtypes = [vp, vp]
+    L.eh_count_range.restype = st
+    L.eh_count_range.argtypes = [vp, st, u32, u32, ctypes.POINTER(ExecOpts), vp, u64p]
+    L.eh_count_range_async.restype = st
+    L.eh_count_range_async.argtypes = [vp, st, u32, u32, ctypes.POINTER(ExecOpts), vp, vp]
+    L.eh_range_bounds.restype = st
+    L.eh_range_bounds.argtypes = [u64p, u64, u32, u32, u64p, u64p]
+    L.eh_trie_stats.restype = st
+    L.eh_trie_stats.argtypes = [vp, ctypes.POINTER(TrieStats)]
     L.eh_count_info_get.restype = st
     L.eh_count_info_get.argtypes = [vp, st, ctypes.POINTER(ExecOpts), vp, ctypes.POINTER(CountInfo)]
     L.eh_trim_memory.restype = st
@@ -185,6 +196,15 @@ def batch_profile():
     return {f: getattr(p, f) for f, _ in BatchProfile._fields_}
 
 
+def range_bounds(cost, part, nparts):
+    """eh_range_bounds: the items [lo, hi) of part `part` of `nparts` of a list
+    with per-item costs `cost` (host-only; the split eh_count_range applies)."""
+    cost = np.ascontiguousarray(cost, np.uint64)
+    lo, hi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().eh_range_bounds(_u64p(cost), len(cost), part, nparts, ctypes.byref(lo), ctypes.byref(hi)))
+    return int(lo.value), int(hi.value)
+
+
 def trim_memory():
     """Return the device temporaries cached in the default memory pool (eh_trim_memory)."""
     _check(lib().eh_trim_memory())
@@ -255,6 +275,19 @@ class Trie:
         _check(lib().eh_count_ex(self._h, _pattern(pattern), sp, sl, xo, _stream(stream), ctypes.byref(out)))
         return int(out.value)
 
+    def count_range(self, pattern, part, nparts, xopts=None, stream=None):
+        """eh_count_range: part `part` of `nparts` of the whole-graph count."""
+        out = ctypes.c_uint64(0)
+        xo = ctypes.byref(xopts) if xopts is not None else None
+        _check(lib().eh_count_range(self._h, _pattern(pattern), part, nparts, xo, _stream(stream),
+                                    ctypes.byref(out)))
+        return int(out.value)
+
+    def count_range_async(self, pattern, part, nparts, d_out_ptr, xopts=None, stream=None):
+        xo = ctypes.byref(xopts) if xopts is not None else None
+        _check(lib().eh_count_range_async(self._h, _pattern(pattern), part, nparts, xo, _stream(stream),
+                                          ctypes.c_void_p(d_out_ptr)))
+
     def count_async(self, pattern, d_out_ptr, xopts=None, stream=None):
         xo = ctypes.byref(xopts) if xopts is not None else None
         _check(lib().eh_count_async(self._h, _pattern(pattern), xo, _stream(stream), ctypes.c_void_p(d_out_ptr)))
@@ -270,7 +303,7 @@ class Trie:
 
     def stats(self):
         s = TrieStats()
-        _check(lib().eh_trie_stats_get(self._h, ctypes.byref(s)))
+        _check(lib().eh_trie_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in TrieStats._fields_ if f != "reserved"}
 
     def count_selected(self, pattern, node, xopts=None, stream=None):

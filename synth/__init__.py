@@ -56,7 +56,7 @@ def lib():
         L.synth_chunglu_weight.restype = ctypes.c_double
         L.synth_chunglu_weight.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.synth_graph_new.restype = ctypes.c_void_p
-        L.synth_graph_new.argtypes = [ctypes.c_uint32, u32p, u32p, ctypes.c_uint64]
+        L.synth_graph_new.argtypes = [ctypes.c_uint32, u32p, u32p, ctypes.c_uint64, ctypes.c_int]
         L.synth_graph_free.argtypes = [ctypes.c_void_p]
         L.synth_graph_degree.restype = ctypes.c_uint64
         L.synth_graph_degree.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
@@ -124,7 +124,7 @@ def ego_subsets(n, src, dst, k, n_queries, mode, lo, hi, nthreads=None):
     induced (simple) edge count reaches floor(lo (hi/lo)^U).  Returns
     (offsets[n_queries+1] uint64, pool uint32) with subsets in BFS order."""
     L = lib()
-    g = L.synth_graph_new(n, _u32p(src), _u32p(dst), len(src))
+    g = L.synth_graph_new(n, _u32p(src), _u32p(dst), len(src), _threads(nthreads))
     if not g:
         raise MemoryError("synth graph")
     try:

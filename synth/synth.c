@@ -256,37 +256,74 @@ static int cmp_u32(const void *x, const void *y) {
     return a < b ? -1 : a > b;
 }
 
-void *synth_graph_new(uint32_t n, const uint32_t *src, const uint32_t *dst, uint64_t n_edges) {
+typedef struct { uint32_t n; const uint32_t *src, *dst; uint64_t *slot; uint32_t *adj; } edge_ctx;
+
+static void edge_count_range(void *p, int64_t lo, int64_t hi, int tid) {
+    (void)tid;
+    edge_ctx *c = (edge_ctx *)p;
+    for (int64_t i = lo; i < hi; ++i) {
+        uint32_t s = c->src[i], t = c->dst[i];
+        if (s == t || s >= c->n || t >= c->n) continue;
+        __atomic_fetch_add(&c->slot[s], 1, __ATOMIC_RELAXED);
+        __atomic_fetch_add(&c->slot[t], 1, __ATOMIC_RELAXED);
+    }
+}
+
+static void edge_fill_range(void *p, int64_t lo, int64_t hi, int tid) {
+    (void)tid;
+    edge_ctx *c = (edge_ctx *)p;
+    for (int64_t i = lo; i < hi; ++i) {
+        uint32_t s = c->src[i], t = c->dst[i];
+        if (s == t || s >= c->n || t >= c->n) continue;
+        c->adj[__atomic_fetch_add(&c->slot[s], 1, __ATOMIC_RELAXED)] = t;
+        c->adj[__atomic_fetch_add(&c->slot[t], 1, __ATOMIC_RELAXED)] = s;
+    }
+}
+
+typedef struct { uint64_t *off; uint32_t *adj; uint64_t *len; } sortlist_ctx;
+
+/* sorts the lists of vertices [lo, hi) in place and drops repeats; the new
+ * length of each list goes to len[v] */
+static void sortlist_range(void *p, int64_t lo, int64_t hi, int tid) {
+    (void)tid;
+    sortlist_ctx *c = (sortlist_ctx *)p;
+    for (int64_t v = lo; v < hi; ++v) {
+        uint64_t b = c->off[v], e = c->off[v + 1], w = b;
+        qsort(c->adj + b, e - b, sizeof(uint32_t), cmp_u32);
+        for (uint64_t i = b; i < e; ++i)
+            if (i == b || c->adj[i] != c->adj[i - 1]) c->adj[w++] = c->adj[i];
+        c->len[v] = w - b;
+    }
+}
+
+void *synth_graph_new(uint32_t n, const uint32_t *src, const uint32_t *dst, uint64_t n_edges, int nthreads) {
     synth_graph *g = (synth_graph *)calloc(1, sizeof(synth_graph));
     if (!g) return NULL;
     g->n = n;
     g->off = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
     uint64_t *fill = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
     if (!g->off || !fill) { free(g->off); free(fill); free(g); return NULL; }
-    for (uint64_t i = 0; i < n_edges; ++i) {
-        if (src[i] == dst[i] || src[i] >= n || dst[i] >= n) continue;
-        g->off[src[i] + 1]++;
-        g->off[dst[i] + 1]++;
-    }
+    /* list lengths, then each edge placed into both lists (atomic slots, so
+     * the order inside a list depends on the threads; the sort below fixes it) */
+    edge_ctx ec = {n, src, dst, g->off + 1, NULL};
+    par_for(nthreads, (int64_t)n_edges, 1 << 16, edge_count_range, &ec);
     for (uint32_t v = 0; v < n; ++v) g->off[v + 1] += g->off[v];
     g->adj = (uint32_t *)malloc(sizeof(uint32_t) * (g->off[n] ? g->off[n] : 1));
     if (!g->adj) { free(g->off); free(fill); free(g); return NULL; }
     memcpy(fill, g->off, sizeof(uint64_t) * ((size_t)n + 1));
-    for (uint64_t i = 0; i < n_edges; ++i) {
-        uint32_t s = src[i], t = dst[i];
-        if (s == t || s >= n || t >= n) continue;
-        g->adj[fill[s]++] = t;
-        g->adj[fill[t]++] = s;
-    }
-    /* sort each list ascending and drop repeats, then repack */
+    ec.slot = fill;
+    ec.adj = g->adj;
+    par_for(nthreads, (int64_t)n_edges, 1 << 16, edge_fill_range, &ec);
+    /* sort each list ascending and drop repeats (in parallel over vertices,
+     * `fill` then holds each list's new length), then repack */
+    sortlist_ctx sc = {g->off, g->adj, fill};
+    par_for(nthreads, (int64_t)n, 4096, sortlist_range, &sc);
     uint64_t w = 0;
     for (uint32_t v = 0; v < n; ++v) {
-        uint64_t b = g->off[v], e = g->off[v + 1];
-        qsort(g->adj + b, e - b, sizeof(uint32_t), cmp_u32);
-        uint64_t start = w;
-        for (uint64_t i = b; i < e; ++i)
-            if (i == b || g->adj[i] != g->adj[i - 1]) g->adj[w++] = g->adj[i];
-        g->off[v] = start;
+        uint64_t b = g->off[v], len = fill[v];
+        if (w != b) memmove(g->adj + w, g->adj + b, sizeof(uint32_t) * len);
+        g->off[v] = w;
+        w += len;
     }
     g->off[n] = w;
     free(fill);

@@ -109,7 +109,7 @@ def main():
         "rmat_s16_ef16": lambda: whole_graph("rmat_s16_ef16", lambda: W.rmat_graph(16, 1503 + 16),
                                              ["triangle", "clique4", "lollipop", "lollipop_distinct", "barbell"],
                                              T),
-        "rmat_s22_ef16": lambda: whole_graph("rmat_s22_ef16", W.rmat22, ["triangle"], T),
+        "rmat_s22_ef16": lambda: whole_graph("rmat_s22_ef16", W.rmat22, ["triangle", "lollipop"], T),
         "chunglu_n1000000_g2.1": lambda: whole_graph("chunglu_n1000000_g2.1", W.chunglu_1m,
                                                      ["triangle", "clique4", "barbell"], T),
         "rmat_s20_ego4096": lambda: ego_batch(T),

@@ -40,6 +40,42 @@ def test_max_over_ranks_and_aggregate():
     assert all(abs(r[2] - 2 * 1000.0 / 0.015) < 1e-6 for r in res)   # both replicas' edges
 
 
+def _part_worker(rank, world, port, q):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    rng = np.random.default_rng(5)
+    cost = np.sort(rng.integers(0, 5000, size=3000))[::-1].astype(np.uint64)   # heaviest first, as the plan
+    per_item = rng.integers(0, 100, size=3000).astype(np.int64)                 # each item's partial count
+    mine = bench.part_count_host(cost, per_item, rank, world)
+    t = bench.sum_over_ranks_(torch.tensor([mine], dtype=torch.int64), world)
+    q.put((rank, mine, int(t.item()), int(per_item.sum())))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_partitioned_count_sums_to_the_whole(world):
+    # each rank counts its cost-balanced range of the work list (the split of
+    # eh_count_range, through the host entry point eh_range_bounds); the one
+    # all-reduce gives every rank the whole count
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_part_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in ps:
+        p.join(timeout=60)
+    total = res[0][3]
+    assert all(r[2] == total for r in res)
+    assert sum(r[1] for r in res) == total
+    assert all(r[1] > 0 for r in res)                           # every rank got work
+
+
 def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max(3.5, 1) == 3.5

@@ -10,6 +10,9 @@ a run stopping at its first failure has run every other test already.
 """
 import ctypes
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -29,10 +32,23 @@ def eh():
 
 
 def noalloc(eh, trie, pattern):
+    """One eh_count_noalloc call with the library's allocation-failure hook
+    armed (any device allocation the call made would fail it) and the
+    device's free memory compared before and after."""
+    import torch
+    L = eh.lib()
     out = ctypes.c_uint64(0)
-    r = eh.lib().eh_count_noalloc(trie.handle, eh.PATTERNS[pattern], None, ctypes.byref(out))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    L.eh_test_fail_alloc_after(0)
+    try:
+        r = L.eh_count_noalloc(trie.handle, eh.PATTERNS[pattern], None, ctypes.byref(out))
+    finally:
+        L.eh_test_fail_alloc_after(-1)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     if r != 0:
-        raise eh.EHError(r, eh.lib().eh_last_error().decode())
+        raise eh.EHError(r, L.eh_last_error().decode())
     return int(out.value)
 
 
@@ -82,3 +98,63 @@ def test_rejects_what_it_cannot_hold(eh):
     with pytest.raises(eh.EHError) as ei:
         noalloc(eh, big, "clique4")
     assert ei.value.status == 1 and "arena" in str(ei.value)
+
+
+def test_matches_the_oracle_directly(eh):
+    import oracle
+    g = W.rmat_graph(13, 1503 + 13)
+    o = oracle.Graph(g["n"], g["src"], g["dst"])
+    trie = eh.Trie(g["src"], g["dst"], g["n"], tau=256)
+    trie.info("triangle")
+    for p in PATS:
+        want = o.count(p, nthreads=4)
+        assert noalloc(eh, trie, p) == want
+        assert noalloc(eh, trie, p) == want
+
+
+def test_block_layout_trie_and_barbell_rejection(eh):
+    g = W.rmat_graph(13, 1503 + 13)
+    blk = eh.Trie(g["src"], g["dst"], g["n"], tau=256, block_layout=True)
+    want = blk.count("triangle")                          # the block-layout kernel; also builds the plan
+    assert noalloc(eh, blk, "triangle") == want            # the set-level kernel, same count
+    assert noalloc(eh, blk, "clique4") == blk.count("clique4")
+    with pytest.raises(eh.EHError) as ei:
+        noalloc(eh, blk, "barbell")
+    assert ei.value.status == 1
+
+
+_FRESH = r"""
+import ctypes, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+import paper_1503_02368_gb300 as eh
+from synth import workloads as W
+torch.cuda.init()
+g = W.rmat_graph(12, 1503 + 12)
+t = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+t.info("triangle")
+L = eh.lib()
+res = []
+for p in ("triangle", "clique4", "lollipop"):
+    torch.cuda.synchronize()
+    f0 = torch.cuda.mem_get_info()[0]
+    out = ctypes.c_uint64(0)
+    L.eh_test_fail_alloc_after(0)
+    r = L.eh_count_noalloc(t.handle, eh.PATTERNS[p], None, ctypes.byref(out))
+    L.eh_test_fail_alloc_after(-1)
+    torch.cuda.synchronize()
+    f1 = torch.cuda.mem_get_info()[0]
+    res.append((p, r, f0 - f1, int(out.value), t.count(p)))
+print(repr(res))
+"""
+
+
+def test_first_call_in_a_fresh_process_allocates_nothing(eh):
+    # the first noalloc call of a process (after a trie build and its work
+    # plan, but no count) must not change the device's free memory
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = eval(r.stdout.strip().splitlines()[-1])
+    for p, status, used, got, want in res:
+        assert status == 0 and used == 0 and got == want, (p, status, used, got, want)

@@ -684,6 +684,7 @@ def headline_config(n, m, world):
     return {"workload": WORKLOAD, "n_vertices": n, "m_unique_edges": m,
             "tau": tuned["tau"] if tuned else 32, "cta_warps": tuned["cta_warps"] if tuned else 8,
             "light_max": tuned["light_max"] if tuned else 32, "gallop_ratio": tuned.get("gallop_ratio", 32) if tuned else 32,
+            "pair_warps": tuned.get("pair_warps", 1) if tuned else 1,
             "tuning": "autotuned (paper_1503_02368_gb300/tuned.json)" if tuned else "fixed",
             "l2": "flushed between timed steps (256 MiB write, outside the events)",
             "parallelism": "1 GPU" if world == 1 else
@@ -758,7 +759,8 @@ def run_eh(args):
     warps = 8 if fixed else cfg0["cta_warps"]
     light_max = 32 if fixed else cfg0["light_max"]
     ratio = 32 if fixed else cfg0["gallop_ratio"]
-    xo = eh.exec_opts(cta_warps=warps, light_max=light_max, gallop_ratio=ratio)
+    pw = 1 if fixed else cfg0["pair_warps"]
+    xo = eh.exec_opts(cta_warps=warps, light_max=light_max, gallop_ratio=ratio, pair_warps=pw)
     trie = eh.Trie(g["src"], g["dst"], g["n"], tau=tau)
     m = trie.stats()["n_edges"]
     info = trie.info("triangle", xopts=xo)
@@ -794,7 +796,7 @@ def run_eh(args):
     ms_max = reduce_max(ms, world, dev)
     value = m / (ms_max / 1e3)          # one whole graph per step, on all ranks together
 
-    roof = roofline(info["alg_bytes"], ms, "k_triangle<0,%d>" % warps)
+    roof = roofline(info["alg_bytes"], ms, "k_triangle<0,%d,%d>" % (warps, pw))
     roof["traffic"] = profile_traffic(os.path.join(ROOT, "paper_1503_02368_gb300", "csrc", "count.cu"))
     hbm = roof["peak"]
     st_ach = info["alg_bytes_stored"] / (ms / 1e3) / 1e9
@@ -872,7 +874,7 @@ def run_eh(args):
 
     if rank == 0:
         cfg = headline_config(g["n"], m, world)
-        cfg.update({"tau": tau, "cta_warps": warps, "light_max": light_max, "gallop_ratio": ratio})
+        cfg.update({"tau": tau, "cta_warps": warps, "light_max": light_max, "gallop_ratio": ratio, "pair_warps": pw})
         if fixed:
             cfg["tuning"] = "fixed"
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,

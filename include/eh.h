@@ -132,12 +132,18 @@ typedef enum {
  * directories (eh_trie_export_blocks); the other patterns use the uint arrays. */
 #define EH_BUILD_BLOCK_LAYOUT 2u
 
-/* Execution knobs for the intersection kernels.  NULL = defaults. */
+/* Execution knobs for the intersection kernels.  NULL = defaults; a field
+ * left 0 takes its default. */
 typedef struct {
     uint32_t gallop_ratio;  /* uint∩uint: gallop when |large| > ratio*|small| (Sec. 4.2's 32:1); default 32 */
-    uint32_t light_max;     /* vertices with |N+(u)| <= light_max run one warp each; default 32 */
+    uint32_t light_max;     /* vertices with |N+(u)| <= light_max run one warp each; default 32 (at most 32) */
     uint32_t cta_warps;     /* warps per CTA for heavy vertices (4, 8 or 16); default 8 */
     uint32_t flags;         /* EH_EXEC_* bits, 0 by default */
+    /* warps per intersection: how many warps of a heavy vertex's CTA share one
+     * pair (u, v), each taking every pair_warps-th step of N+(v) against the
+     * staged N+(u) (1, 2 or 4; default 1).  Whole-graph triangle and lollipop
+     * counts; the other patterns take one warp per pair. */
+    uint32_t pair_warps;
 } eh_exec_opts;
 
 /* eh_list staging of A = N+(u) for vertices taken by a whole CTA: by default

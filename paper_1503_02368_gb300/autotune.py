@@ -2,7 +2,8 @@
 
 Searches the set-level bitset threshold tau (Sec. 4.4's rule, which fixes the
 stored layouts, so each value needs its own trie) and the execution knobs
-(warps per CTA for heavy vertices, the light/heavy split) on a workload, by
+(warps per CTA for heavy vertices, the light/heavy split, the warps per
+intersection) on a workload, by
 timing the real kernels through the C ABI, and writes the best setting per
 graph class to a JSON file.  Counts must agree across every setting tried;
 the tuner checks that too, since layouts and launch shapes change speed only.
@@ -18,6 +19,7 @@ from . import eh as _eh
 DEFAULT_TAUS = (8, 32, 128)
 DEFAULT_WARPS = (4, 8, 16)
 DEFAULT_LIGHT = (8, 16, 32)
+DEFAULT_PAIR_WARPS = (1, 2, 4)
 TUNED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -64,8 +66,9 @@ def tune_batch(graph, patterns, offsets, pool, taus=DEFAULT_TAUS, warps=DEFAULT_
 
 
 def tune_whole(graph, pattern="triangle", taus=DEFAULT_TAUS, warps=DEFAULT_WARPS, light=DEFAULT_LIGHT, reps=3,
-               log=None, ratios=(32,)):
-    """Best (tau, cta_warps, light_max, gallop_ratio) for a whole-graph count."""
+               log=None, ratios=(32,), pair_warps=DEFAULT_PAIR_WARPS):
+    """Best (tau, cta_warps, light_max, gallop_ratio, pair_warps) for a
+    whole-graph count; pair_warps is the warps per intersection."""
     import torch
     trials = []
     ref = None
@@ -75,17 +78,19 @@ def tune_whole(graph, pattern="triangle", taus=DEFAULT_TAUS, warps=DEFAULT_WARPS
         for w in warps:
             for lm in light:
                 for r in ratios:
-                    xo = _eh.exec_opts(cta_warps=w, light_max=lm, gallop_ratio=r)
-                    t = _time(lambda: trie.count_async(pattern, out.data_ptr(), xopts=xo), reps)
-                    trie.status()
-                    c = int(out.item())
-                    if ref is None:
-                        ref = c
-                    if c != ref:
-                        raise RuntimeError("counts differ between tuning settings")
-                    trials.append({"tau": tau, "cta_warps": w, "light_max": lm, "gallop_ratio": r, "seconds": t})
-                    if log:
-                        log(trials[-1])
+                    for pw in pair_warps:
+                        xo = _eh.exec_opts(cta_warps=w, light_max=lm, gallop_ratio=r, pair_warps=pw)
+                        t = _time(lambda: trie.count_async(pattern, out.data_ptr(), xopts=xo), reps)
+                        trie.status()
+                        c = int(out.item())
+                        if ref is None:
+                            ref = c
+                        if c != ref:
+                            raise RuntimeError("counts differ between tuning settings")
+                        trials.append({"tau": tau, "cta_warps": w, "light_max": lm, "gallop_ratio": r,
+                                       "pair_warps": pw, "seconds": t})
+                        if log:
+                            log(trials[-1])
         trie.close()
     best = min(trials, key=lambda r: r["seconds"])
     return best, trials
@@ -106,3 +111,38 @@ def load(graph_class, path=TUNED_PATH):
         return None
     with open(path) as f:
         return json.load(f).get(graph_class, {}).get("best")
+
+
+def main(argv=None):
+    """python -m paper_1503_02368_gb300.autotune [rmat_s22_triangle|rmat_s20_ego4096]:
+    searches the named workload on the current GPU and stores the best setting."""
+    import argparse
+    import sys
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["rmat_s22_triangle", "rmat_s20_ego4096"])
+    ap.add_argument("--taus", default=None)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from synth import workloads as W
+
+    def log(r):
+        print(json.dumps(r), flush=True)
+
+    if a.workload == "rmat_s22_triangle":
+        taus = tuple(int(x) for x in a.taus.split(",")) if a.taus else (256, 1024)
+        best, trials = tune_whole(W.rmat22(), "triangle", taus=taus, warps=(8, 16), light=(16, 32),
+                                  reps=a.reps, log=log)
+    else:
+        g = W.rmat20_ego_batch()
+        pats = ["clique4" if p else "triangle" for p in g["patterns"]]
+        taus = tuple(int(x) for x in a.taus.split(",")) if a.taus else (8, 32, 128)
+        best, trials = tune_batch(g, pats, g["offsets"], g["pool"], taus=taus, reps=min(a.reps, 2), log=log)
+    save(a.workload, best, trials)
+    print("best", json.dumps(best))
+
+
+if __name__ == "__main__":
+    main()

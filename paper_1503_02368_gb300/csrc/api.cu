@@ -171,11 +171,13 @@ eh_exec_opts eh_exec_defaults(const eh_exec_opts *x) {
     o.light_max = 32;
     o.cta_warps = 8;
     o.flags = 0;
+    o.pair_warps = 1;
     if (x) {
         if (x->gallop_ratio) o.gallop_ratio = x->gallop_ratio;
         if (x->light_max) o.light_max = std::min<uint32_t>(x->light_max, 32u);
         if (x->cta_warps == 4 || x->cta_warps == 8 || x->cta_warps == 16) o.cta_warps = x->cta_warps;
         o.flags = x->flags;
+        if (x->pair_warps == 2 || x->pair_warps == 4) o.pair_warps = x->pair_warps;
     }
     return o;
 }

@@ -256,14 +256,16 @@ __device__ __forceinline__ void bitmap_plan(const TrieView &tv, uint32_t a_lo, u
     end = dv.len;
 }
 
-template <int MODE>
+// PW warps share one pair: this warp takes part `part` of B's range (every
+// PW-th step of 128 words or 256 elements)
+template <int MODE, int PW = 1>
 __device__ __forceinline__ void run_plan(const TrieView &tv, const uint32_t *sA, uint32_t a_lo, uint32_t a_nw,
                                          uint32_t kind, int64_t base, uint32_t begin, uint32_t end, uint32_t duv,
-                                         Acc &acc, unsigned long long *vt) {
+                                         Acc &acc, unsigned long long *vt, uint32_t part = 0) {
     const uint32_t lane4 = (threadIdx.x & 31) * 4;
     if (kind == 1) {
         const uint32_t *bw = tv.words + base;
-        for (uint32_t i = begin + lane4; i < end; i += 128) {
+        for (uint32_t i = begin + part * 128 + lane4; i < end; i += 128 * PW) {
             const uint4 b = ldg4(bw + i);
             const uint4 a = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
             on_word<MODE>(acc, a.x & b.x, i * 32, duv, tv, vt);
@@ -274,7 +276,7 @@ __device__ __forceinline__ void run_plan(const TrieView &tv, const uint32_t *sA,
     } else if (kind == 2) {
         const uint32_t *bp = tv.nbr + base;
         const uint32_t abase = a_lo * 32, nbits = a_nw * 32;
-        for (uint32_t p = lane4; p < end; p += 256) {
+        for (uint32_t p = part * 256 + lane4; p < end; p += 256 * PW) {
             const uint4 e0 = ldg4(bp + p);
             const uint4 e1 = p + 128 < end ? ldg4(bp + p + 128) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
             const uint32_t w[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
@@ -353,29 +355,34 @@ __device__ __forceinline__ uint32_t next_j(uint32_t *s_next, uint32_t batch = PA
     return __shfl_sync(FULL, j, 0);
 }
 
-template <int MODE, int WARPS>
+// Warps per intersection: with PW > 1 the warps of the CTA take work units
+// (pair j, part p), p < PW, so that PW warps share each pair's B against the
+// on-chip bitmap (every PW-th step of its range each, run_plan); the other
+// dispatches run the whole pair in part 0.  PW = 1 is one pair per warp.
+template <int MODE, int WARPS, int PW = 1>
 __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32_t ratio, uint32_t *sA,
                                           uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
                                           uint32_t *status, unsigned long long *vt) {
     const int lane = threadIdx.x & 31;
     const SetDesc du = tv.desc[u];
-    if (threadIdx.x == 0) *s_next = 1;
+    if (threadIdx.x == 0) *s_next = PW;   // the first unit of pair 1
     StagedA st;
     if (!stage_set<WARPS>(tv, du, sA, mbar, phase, st, status)) return false;
+    const uint32_t n_units = st.len * PW;
     for (;;) {
-        const uint32_t j0 = next_j(s_next);
-        if (j0 >= st.len) break;
-        // the next PAIR_BATCH pairs: v and its descriptor loaded one per lane
-        const uint32_t jl = j0 + lane;
+        const uint32_t j0 = next_j(s_next);   // first unit of this grab
+        if (j0 >= n_units) break;
+        // the next PAIR_BATCH units: their pair's v and descriptor loaded one per lane
+        const uint32_t jl = (j0 + lane) / PW;
         uint32_t vl = 0;
         SetDesc mine = empty_desc();
         if (lane < PAIR_BATCH && jl < st.len) {
             vl = st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl];
             mine = tv.desc[vl];
         }
-        const uint32_t nb = min(PAIR_BATCH, st.len - j0);
+        const uint32_t nb = min(PAIR_BATCH, n_units - j0);
         if (st.amode == 0 && MODE != M_VERTEX) {
-            // each descriptor lane plans its pair; the warp runs the plans in turn
+            // each descriptor lane plans its unit's pair; the warp runs the plans in turn
             uint32_t pk, pb, pe;
             int64_t pbase;
             bitmap_plan(tv, st.a_lo, st.a_nw, mine, pk, pbase, pb, pe);
@@ -383,14 +390,15 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
             for (uint32_t i = 0; i < nb; ++i) {
                 const uint32_t kind = __shfl_sync(FULL, pk, i);
                 if (kind == 0) continue;
-                run_plan<MODE>(tv, sA, st.a_lo, st.a_nw, kind, __shfl_sync(FULL, pbase, i),
-                               __shfl_sync(FULL, pb, i), __shfl_sync(FULL, pe, i),
-                               MODE == M_LOLLI ? __shfl_sync(FULL, pduv, i) : 0u, acc, vt);
+                run_plan<MODE, PW>(tv, sA, st.a_lo, st.a_nw, kind, __shfl_sync(FULL, pbase, i),
+                                   __shfl_sync(FULL, pb, i), __shfl_sync(FULL, pe, i),
+                                   MODE == M_LOLLI ? __shfl_sync(FULL, pduv, i) : 0u, acc, vt, (j0 + i) % PW);
             }
             continue;
         }
         for (uint32_t i = 0; i < nb; ++i) {
-            const uint32_t j = j0 + i;
+            if ((j0 + i) % PW != 0) continue;   // the whole pair runs in its first unit
+            const uint32_t j = (j0 + i) / PW;
             const uint32_t v = __shfl_sync(FULL, vl, i);
             const SetDesc dv = bcast_desc(mine, i);
             if (dv.len == 0) continue;
@@ -413,7 +421,7 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
 }
 
 // counters[0]: next heavy item, counters[1]: next light chunk
-template <int MODE, int WARPS>
+template <int MODE, int WARPS, int PW = 1>
 __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint32_t *__restrict__ heavy, uint32_t n_heavy,
                                                          const uint32_t *__restrict__ light, uint32_t n_light,
                                                          uint32_t ratio, unsigned long long *counters,
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
         const unsigned long long t0 = acc.t;
-        if (!tri_heavy<MODE, WARPS>(tv, heavy[item], ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
+        if (!tri_heavy<MODE, WARPS, PW>(tv, heavy[item], ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
         if (MODE == M_APEX) {   // this vertex's triangles (as the largest id) to vt[item]
             unsigned long long d = acc.t - t0;
             for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
@@ -996,11 +1004,11 @@ eh_status launch_k4(eh_trie *t, const WorkPlan &plan, TrieView tv, const eh_exec
     return EH_OK;
 }
 
-template <int MODE, int WARPS>
+template <int MODE, int WARPS, int PW = 1>
 eh_status launch_tri(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
                      unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status,
                      unsigned long long *d_vt) {
-    auto kern = k_triangle<MODE, WARPS>;
+    auto kern = k_triangle<MODE, WARPS, PW>;
     const int smem = BM_CAP_WORDS * 4;
     static bool attr_set = false;
     if (!attr_set) {
@@ -1018,15 +1026,28 @@ eh_status launch_tri(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, 
     return EH_OK;
 }
 
+template <int MODE, int PW>
+eh_status launch_tri_pw(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
+                        unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status,
+                        unsigned long long *d_vt) {
+    switch (xo.cta_warps) {
+        case 4: return launch_tri<MODE, 4, PW>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        case 16: return launch_tri<MODE, 16, PW>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        default: return launch_tri<MODE, 8, PW>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+    }
+}
+
+// warps per intersection (xo.pair_warps 1, 2 or 4) for the count and the
+// lollipop; the per-vertex modes take one warp per pair
 template <int MODE>
 eh_status launch_tri_w(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, cudaStream_t s,
                        unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status,
                        unsigned long long *d_vt) {
-    switch (xo.cta_warps) {
-        case 4: return launch_tri<MODE, 4>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
-        case 16: return launch_tri<MODE, 16>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
-        default: return launch_tri<MODE, 8>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+    if (MODE == M_COUNT || MODE == M_LOLLI) {
+        if (xo.pair_warps == 2) return launch_tri_pw<MODE, 2>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
+        if (xo.pair_warps == 4) return launch_tri_pw<MODE, 4>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
     }
+    return launch_tri_pw<MODE, 1>(plan, tv, xo, s, d_acc, d_counters, d_status, d_vt);
 }
 
 }  // namespace

@@ -36,7 +36,7 @@ class BuildOpts(ctypes.Structure):
 
 class ExecOpts(ctypes.Structure):
     _fields_ = [("gallop_ratio", ctypes.c_uint32), ("light_max", ctypes.c_uint32), ("cta_warps", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("pair_warps", ctypes.c_uint32)]
 
 
 class TrieStats(ctypes.Structure):
@@ -219,8 +219,8 @@ EH_EXEC_SORTED_A = 1
 EH_EXEC_GLOBAL_A = 2
 
 
-def exec_opts(gallop_ratio=0, light_max=0, cta_warps=0, flags=0):
-    return ExecOpts(gallop_ratio, light_max, cta_warps, flags)
+def exec_opts(gallop_ratio=0, light_max=0, cta_warps=0, flags=0, pair_warps=0):
+    return ExecOpts(gallop_ratio, light_max, cta_warps, flags, pair_warps)
 
 
 def _pattern(p):

@@ -23,6 +23,7 @@ def test_committed_choices_are_valid():
         b = autotune.load(cls)
         assert b is not None
         assert b["cta_warps"] in (4, 8, 16) and 1 <= b["light_max"] <= 32 and b["tau"] >= 0
+        assert b.get("pair_warps", 1) in (1, 2, 4)
 
 
 @pytest.mark.gpu
@@ -30,8 +31,10 @@ def test_tuning_search_keeps_counts():
     import synth
     from synth import workloads as W
     g = W.rmat_graph(12, 1503 + 12)
-    best, trials = autotune.tune_whole(g, "triangle", taus=(0, 32), warps=(4, 8), light=(8, 32), reps=1)
-    assert len(trials) == 8 and best in trials
+    best, trials = autotune.tune_whole(g, "triangle", taus=(0, 32), warps=(4, 8), light=(8, 32), reps=1,
+                                       pair_warps=(1, 4))
+    assert len(trials) == 16 and best in trials
+    assert {t["pair_warps"] for t in trials} == {1, 4}
     off, pool = synth.ego_subsets(g["n"], g["src"], g["dst"], synth.key(9, 9), 16, 0, 8, 512)
     best, trials = autotune.tune_batch(g, ["triangle", "clique4"] * 8, off, pool, taus=(8,), warps=(8,),
                                        light=(16, 32), reps=1)

@@ -151,7 +151,9 @@ def test_layout_independence_rmat(eh, tau):
 
 
 @pytest.mark.parametrize("xo", [dict(gallop_ratio=1), dict(gallop_ratio=1000), dict(light_max=2),
-                                dict(light_max=8, cta_warps=4), dict(cta_warps=16), dict(light_max=32)])
+                                dict(light_max=8, cta_warps=4), dict(cta_warps=16), dict(light_max=32),
+                                dict(pair_warps=2), dict(pair_warps=4), dict(pair_warps=4, cta_warps=4),
+                                dict(pair_warps=2, cta_warps=16, light_max=8)])
 def test_exec_knobs_do_not_change_counts(eh, xo):
     g = W.rmat_graph(12, 1503 + 12)
     o = oracle.Graph(g["n"], g["src"], g["dst"])
@@ -177,6 +179,26 @@ def test_hub_graph_spans_many_tiles(eh):
         t = eh.Trie(s, d, n, tau=tau)
         for p in PATS:
             assert t.count(p) == o.count(p, nthreads=8), (p, tau)
+
+
+@pytest.mark.parametrize("pw", [1, 2, 4])
+def test_warps_per_intersection_on_hub_graphs(eh, pw):
+    # pairs (u, v) with N+(v) spanning many 128-word / 256-element steps, shared by
+    # 1, 2 or 4 warps: every split must give the oracle's count
+    rng = np.random.default_rng(11)
+    n = 40000
+    e = [(int(h), int(v)) for h in range(40) for v in rng.choice(np.arange(40, n), 2500, replace=False)]
+    e += [(int(a), int(b)) for a, b in rng.integers(0, 400, size=(30000, 2))]
+    s, d = G.arrays(e)
+    o = oracle.Graph(n, s, d)
+    want = {p: o.count(p, nthreads=8) for p in ("triangle", "lollipop", "lollipop_distinct")}
+    for tau in (0, 32, 1024, 0xFFFFFFFF):
+        t = eh.Trie(s, d, n, tau=tau)
+        for w in (4, 8, 16):
+            x = eh.exec_opts(pair_warps=pw, cta_warps=w)
+            for p, c in want.items():
+                assert t.count(p, xopts=x) == c, (p, tau, w, pw)
+        t.close()
 
 
 def test_vertex_triangles_small(eh):

@@ -404,14 +404,17 @@ eh_status eh_count_batch_ex(const eh_trie *trie, const eh_query *queries, uint32
 /* Where the calling thread's last eh_count_batch / eh_count_batch_ex spent
  * its time, summed over its device batches: prepare = subsets to device,
  * sort, membership bitmaps, induced sub-tries, layouts, work lists (host wall
- * clock, stream synchronised); count = the persistent count launch and the
- * result copy. */
+ * clock, stream synchronised); count = the persistent count launch (a CUDA
+ * graph) and the result copy.  graph_reuses = device batches whose count
+ * graph was launched by updating the calling thread's executable graph in
+ * place instead of instantiating a new one. */
 typedef struct {
     uint64_t queries, batches;
     uint64_t sub_vertices;      /* distinct (query, vertex) pairs */
     uint64_t sub_set_elements;  /* padded elements of the induced pruned sets */
     uint64_t heavy_items, light_items;
     double prepare_s, count_s;
+    uint64_t graph_reuses;
 } eh_batch_profile;
 
 eh_status eh_batch_profile_get(eh_batch_profile *out);

@@ -73,6 +73,10 @@ eh_status check_status(eh_trie *t, cudaStream_t s) {
     if (st & DEV_ST_OVERFLOW) { eh_set_error("count exceeds uint64"); return EH_EOVERFLOW; }
     if (st & DEV_ST_INVALID) { eh_set_error("invalid id on the device"); return EH_EINVAL; }
     if (st & DEV_ST_RANGE) { eh_set_error("listing: the count and write passes disagree"); return EH_ECUDA; }
+    if (st & DEV_ST_BOUNDS) {
+        eh_set_error("a device load fell outside its array (checked build; the load was not made)");
+        return EH_ECUDA;
+    }
     return EH_OK;
 }
 

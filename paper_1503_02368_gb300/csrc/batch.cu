@@ -388,6 +388,10 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     BatchView bv;
     bv.desc = desc; bv.nbr = nbr; bv.words = words; bv.deg = deg; bv.sub_q = sub_q; bv.qbase = qbase;
     bv.qpat = d_qpat;
+    bv.n_sub = V;
+    bv.n_nbr = total;
+    bv.n_words = n_words;
+    bv.n_queries = nq;
 
     // 5. work lists
     uint64_t *cost = nullptr;
@@ -422,13 +426,22 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     EH_TRY(sc.alloc(&d_out, 2ull * nq));
     EH_TRY(sc.alloc(&d_cnt, 2));
     EH_TRY(sc.alloc(&d_bst, 1));
-    EH_CUDA_TRY(cudaStreamSynchronize(s));   // every buffer above is ready
     // The count phase (clears + the one persistent launch) is captured in a
-    // CUDA graph on this thread's capture stream and launched as a graph.
+    // CUDA graph on this thread's capture stream and launched as a graph.  The
+    // thread keeps one executable graph: each batch's capture updates it in
+    // place (cudaGraphExecUpdate: same nodes, new launch parameters), and it is
+    // instantiated again only when the update is refused.  The batches of a
+    // thread run one after another (each ends with a synchronisation), so the
+    // executable graph is idle whenever it is updated.
     static thread_local cudaStream_t cs = nullptr;
+    static thread_local cudaEvent_t ready = nullptr;
+    static thread_local cudaGraphExec_t gexec = nullptr;
     if (!cs) EH_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (!ready) EH_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    // every buffer above is ready on `s`: the capture stream waits for it on the device
+    EH_CUDA_TRY(cudaEventRecord(ready, s));
+    EH_CUDA_TRY(cudaStreamWaitEvent(cs, ready, 0));
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
     EH_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     eh_status lst = EH_OK;
     if (cudaMemsetAsync(d_out, 0, 16ull * nq, cs) != cudaSuccess || cudaMemsetAsync(d_bst, 0, 4, cs) != cudaSuccess)
@@ -443,7 +456,18 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
         if (lst == EH_OK) eh_set_error("batch graph capture: %s", cudaGetErrorString(ce));
         return lst != EH_OK ? lst : EH_ECUDA;
     }
-    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    ce = cudaSuccess;
+    if (gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(gexec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+        } else {
+            g_prof.graph_reuses += 1;
+        }
+    }
+    if (!gexec) ce = cudaGraphInstantiate(&gexec, graph, 0);
     if (ce == cudaSuccess) ce = cudaGraphLaunch(gexec, cs);
     std::vector<unsigned long long> h_out(2ull * nq);
     std::vector<uint32_t> h_stat(nq);
@@ -452,8 +476,11 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_stat.data(), d_qstat, 4ull * nq, cudaMemcpyDeviceToHost, cs);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&bst, d_bst, 4, cudaMemcpyDeviceToHost, cs);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
-    if (gexec) cudaGraphExecDestroy(gexec);
     cudaGraphDestroy(graph);
+    if (ce != cudaSuccess && gexec) {
+        cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    }
     if (ce != cudaSuccess) {
         eh_set_error("batch count graph: %s", cudaGetErrorString(ce));
         return EH_ECUDA;

@@ -26,6 +26,41 @@ namespace {
 
 using namespace ehd;
 
+// the checked build's per-CTA table of the arrays a count kernel reads
+// (thread 0, before the kernel's first barrier)
+#ifdef EH_CHECK_LOADS
+__device__ __forceinline__ void chk_trie(const TrieView &tv, const uint32_t *heavy, uint32_t nh, const uint32_t *light,
+                                         uint32_t nl, uint32_t *status) {
+    chk_reset(status);
+    chk_add(tv.nbr, tv.n_nbr * 4);
+    chk_add(tv.words, tv.n_words * 4);
+    chk_add(tv.deg, (uint64_t)tv.n * 4);
+    chk_add(tv.desc, (uint64_t)tv.n * sizeof(SetDesc));
+    chk_add(heavy, (uint64_t)nh * 4);
+    chk_add(light, (uint64_t)nl * 4);
+}
+__device__ __forceinline__ void chk_batch(const BatchView &b, const uint32_t *heavy, uint32_t nh,
+                                          const uint32_t *light, uint32_t nl, uint32_t *status) {
+    chk_reset(status);
+    chk_add(b.desc, b.n_sub * sizeof(SetDesc));
+    chk_add(b.nbr, b.n_nbr * 4);
+    chk_add(b.words, b.n_words * 4);
+    chk_add(b.deg, b.n_sub * 4);
+    chk_add(b.sub_q, b.n_sub * 4);
+    chk_add(b.qbase, (b.n_queries + 1) * 4);
+    chk_add(b.qpat, b.n_queries * 4);
+    chk_add(heavy, (uint64_t)nh * 4);
+    chk_add(light, (uint64_t)nl * 4);
+}
+#define CHK_TRIE(tv, h, nh, l, nl, st) chk_trie(tv, h, nh, l, nl, st)
+#define CHK_BATCH(b, h, nh, l, nl, st) chk_batch(b, h, nh, l, nl, st)
+#define CHK_ADD(p, bytes) chk_add(p, bytes)
+#else
+#define CHK_TRIE(tv, h, nh, l, nl, st) ((void)0)
+#define CHK_BATCH(b, h, nh, l, nl, st) ((void)0)
+#define CHK_ADD(p, bytes) ((void)0)
+#endif
+
 constexpr uint32_t BM_CAP_WORDS = 8192;        // 32 KB on-chip bitmap: value ranges up to 262,144
 
 enum { M_COUNT = 0, M_LOLLI = 1, M_VERTEX = 2, M_APEX = TRI_MODE_APEX };
@@ -41,7 +76,7 @@ template <int MODE>
 __device__ __forceinline__ void on_match(Acc &acc, uint32_t w, uint32_t duv, const TrieView &tv,
                                          unsigned long long *vt) {
     acc.t += 1;
-    if (MODE == M_LOLLI) acc.s += duv + __ldg(&tv.deg[w]);
+    if (MODE == M_LOLLI) acc.s += duv + ldg1(&tv.deg[w]);
     if (MODE == M_VERTEX) atomicAdd(&vt[w], 1ull);
 }
 
@@ -108,17 +143,17 @@ __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *
         const uint32_t *bw = tv.words + dv.woff;
         const uint32_t base = dv.lo_word * 32, nbits = dv.nwords * 32;
         for (uint32_t i = lane; i < j; i += 32) {
-            uint32_t a = A[i], x = a - base;
-            if (x < nbits && ((__ldg(&bw[x >> 5]) >> (x & 31)) & 1u)) on_match<MODE>(acc, a, duv, tv, vt);
+            uint32_t a = ld_any(&A[i]), x = a - base;
+            if (x < nbits && ((ldg1(&bw[x >> 5]) >> (x & 31)) & 1u)) on_match<MODE>(acc, a, duv, tv, vt);
         }
         return;
     }
     const uint32_t *B = tv.nbr + dv.off;
     if ((uint64_t)dv.len > (uint64_t)ratio * j) {   // galloping side: search A's elements in B
         for (uint32_t i = lane; i < j; i += 32) {
-            uint32_t a = A[i];
+            uint32_t a = ld_any(&A[i]);
             uint32_t pos = lower_bound(B, 0, dv.len, a);
-            if (pos < dv.len && __ldg(&B[pos]) == a) on_match<MODE>(acc, a, duv, tv, vt);
+            if (pos < dv.len && ldg1(&B[pos]) == a) on_match<MODE>(acc, a, duv, tv, vt);
         }
         return;
     }
@@ -140,7 +175,7 @@ __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *
         uint32_t w[4] = {e.x, e.y, e.z, e.w};
         if (hi - lo <= 8) {
             for (uint32_t i = lo; i < hi; ++i) {
-                uint32_t a = A[i];
+                uint32_t a = ld_any(&A[i]);
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (w[k] == a) on_match<MODE>(acc, a, duv, tv, vt);
@@ -150,7 +185,7 @@ __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *
             for (int k = 0; k < 4; ++k) {
                 if (w[k] == EH_PAD) continue;
                 uint32_t pos = lower_bound(A, lo, hi, w[k]);
-                if (pos < hi && A[pos] == w[k]) on_match<MODE>(acc, w[k], duv, tv, vt);
+                if (pos < hi && ld_any(&A[pos]) == w[k]) on_match<MODE>(acc, w[k], duv, tv, vt);
             }
         }
     }
@@ -164,13 +199,13 @@ __device__ __forceinline__ bool light_match(const TrieView &tv, uint32_t a, uint
     const bool act = (uint32_t)lane < eff;
     if (dB.nwords && eff <= dB.len) {   // uint ∩ bitset: probe one bit
         uint32_t x = a - dB.lo_word * 32;
-        return act && x < dB.nwords * 32 && ((__ldg(&tv.words[dB.woff + (x >> 5)]) >> (x & 31)) & 1u);
+        return act && x < dB.nwords * 32 && ((ldg1(&tv.words[dB.woff + (x >> 5)]) >> (x & 31)) & 1u);
     }
     const uint32_t *B = tv.nbr + dB.off;
     if ((uint64_t)dB.len > (uint64_t)ratio * eff) {   // galloping side: binary search in B
         if (!act) return false;
         uint32_t pos = lower_bound(B, 0, dB.len, a);
-        return pos < dB.len && __ldg(&B[pos]) == a;
+        return pos < dB.len && ldg1(&B[pos]) == a;
     }
     // merge side: B in 128-element chunks against the lanes whose value falls in the chunk's span
     bool hit = false;
@@ -196,23 +231,30 @@ __device__ __forceinline__ bool light_match(const TrieView &tv, uint32_t a, uint
 template <int MODE>
 __device__ void light_vertex(const TrieView &tv, uint32_t u, uint32_t ratio, Acc &acc, unsigned long long *vt) {
     const int lane = threadIdx.x & 31;
-    const SetDesc du = tv.desc[u];
+    const SetDesc du = ld_desc(&tv.desc[u]);
     const uint32_t k = du.len;
-    const uint32_t a = lane < k ? __ldg(&tv.nbr[du.off + lane]) : EH_PAD;
-    const SetDesc mine = (lane >= 1 && lane < k) ? tv.desc[a] : empty_desc();
+    const uint32_t a = lane < k ? ldg1(&tv.nbr[du.off + lane]) : EH_PAD;
+    const SetDesc mine = (lane >= 1 && lane < k) ? ld_desc(&tv.desc[a]) : empty_desc();
+    // per-vertex triangle counts: each lane counts the triangles of its own
+    // element a (as the lowest vertex w, or as v when its pair is processed),
+    // lane 0 those of u; one atomic per element and vertex at the end
+    unsigned long long mine_t = 0, u_t = 0;
     for (uint32_t j = 1; j < k; ++j) {
-        const uint32_t v = __shfl_sync(FULL, a, j);
         const SetDesc dv = bcast_desc(mine, j);
         if (dv.len == 0) continue;
         const bool hit = light_match(tv, a, j, dv, ratio);
-        if (hit) on_match<MODE>(acc, a, du.deg + dv.deg, tv, vt);
         if (MODE == M_VERTEX) {
-            uint32_t pc = __popc(__ballot_sync(FULL, hit));
-            if (lane == 0 && pc) {
-                atomicAdd(&vt[u], (unsigned long long)pc);
-                atomicAdd(&vt[v], (unsigned long long)pc);
-            }
+            const uint32_t pc = __popc(__ballot_sync(FULL, hit));
+            acc.t += hit ? 1u : 0u;
+            mine_t += (hit ? 1u : 0u) + ((uint32_t)lane == j ? pc : 0u);
+            u_t += pc;
+        } else if (hit) {
+            on_match<MODE>(acc, a, du.deg + dv.deg, tv, vt);
         }
+    }
+    if (MODE == M_VERTEX) {
+        if ((uint32_t)lane < k && mine_t) atomicAdd(&vt[a], mine_t);
+        if (lane == 0 && u_t) atomicAdd(&vt[u], u_t);
     }
 }
 
@@ -297,11 +339,11 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
     const int tid = threadIdx.x;
     st.len = du.len;
     st.Ag = tv.nbr + du.off;
-    const uint32_t first = __ldg(&st.Ag[0]), last = __ldg(&st.Ag[st.len - 1]);
+    const uint32_t first = ldg1(&st.Ag[0]), last = ldg1(&st.Ag[st.len - 1]);
     st.a_lo = (first >> 7) << 2;
     st.a_nw = (((last >> 5) + 1 - st.a_lo) + 3) & ~3u;
     bool copy = false;
-    if (du.nwords && du.nwords <= BM_CAP_WORDS) {
+    if (du.nwords && du.nwords <= BM_CAP_WORDS && bulk_src_ok(tv.words + du.woff, du.nwords * 4)) {
         st.amode = 0;
         st.a_lo = du.lo_word;
         st.a_nw = du.nwords;
@@ -317,10 +359,10 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
             *reinterpret_cast<uint4 *>(sA + i) = make_uint4(0, 0, 0, 0);
         __syncthreads();
         for (uint32_t i = tid; i < st.len; i += WARPS * 32) {
-            uint32_t x = __ldg(&st.Ag[i]);
+            uint32_t x = ldg1(&st.Ag[i]);
             atomicOr(&sA[(x >> 5) - st.a_lo], 1u << (x & 31));
         }
-    } else if (st.len <= BM_CAP_WORDS) {
+    } else if (st.len <= BM_CAP_WORDS && bulk_src_ok(st.Ag, ((st.len + 3) & ~3u) * 4)) {
         st.amode = 1;
         copy = true;
         if (tid == 0) {
@@ -364,11 +406,12 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
                                           uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
                                           uint32_t *status, unsigned long long *vt) {
     const int lane = threadIdx.x & 31;
-    const SetDesc du = tv.desc[u];
+    const SetDesc du = ld_desc(&tv.desc[u]);
     if (threadIdx.x == 0) *s_next = PW;   // the first unit of pair 1
     StagedA st;
     if (!stage_set<WARPS>(tv, du, sA, mbar, phase, st, status)) return false;
     const uint32_t n_units = st.len * PW;
+    const unsigned long long t_start = acc.t;   // u's triangles, added once per vertex (per-vertex mode)
     for (;;) {
         const uint32_t j0 = next_j(s_next);   // first unit of this grab
         if (j0 >= n_units) break;
@@ -377,8 +420,8 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
         uint32_t vl = 0;
         SetDesc mine = empty_desc();
         if (lane < PAIR_BATCH && jl < st.len) {
-            vl = st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl];
-            mine = tv.desc[vl];
+            vl = st.amode == 0 ? ldg1(&st.Ag[jl]) : ld_any(&st.A[jl]);
+            mine = ld_desc(&tv.desc[vl]);
         }
         const uint32_t nb = min(PAIR_BATCH, n_units - j0);
         if (st.amode == 0 && MODE != M_VERTEX) {
@@ -409,12 +452,14 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
             if (MODE == M_VERTEX) {
                 unsigned long long pc = acc.t - t0;
                 for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
-                if (lane == 0 && pc) {
-                    atomicAdd(&vt[u], pc);
-                    atomicAdd(&vt[v], pc);
-                }
+                if (lane == 0 && pc) atomicAdd(&vt[v], pc);
             }
         }
+    }
+    if (MODE == M_VERTEX) {
+        unsigned long long tu = acc.t - t_start;
+        for (int d = 16; d > 0; d >>= 1) tu += __shfl_xor_sync(FULL, tu, d);
+        if (lane == 0 && tu) atomicAdd(&vt[u], tu);
     }
     __syncthreads();
     return true;
@@ -434,7 +479,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
     const int tid = threadIdx.x, lane = tid & 31;
     Acc acc{0, 0};
     uint32_t phase = 0;
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        CHK_TRIE(tv, heavy, n_heavy, light, n_light, status);
+    }
     __syncthreads();
 
     // heavy vertices: one CTA each
@@ -444,7 +492,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
         const unsigned long long t0 = acc.t;
-        if (!tri_heavy<MODE, WARPS, PW>(tv, heavy[item], ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
+        if (!tri_heavy<MODE, WARPS, PW>(tv, ldg1(&heavy[item]), ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
         if (MODE == M_APEX) {   // this vertex's triangles (as the largest id) to vt[item]
             unsigned long long d = acc.t - t0;
             for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
@@ -467,7 +515,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
         for (uint32_t i = (uint32_t)base; i < end; ++i) {
             const unsigned long long t0 = acc.t;
-            light_vertex<MODE>(tv, __ldg(&light[i]), ratio, acc, vt);
+            light_vertex<MODE>(tv, ldg1(&light[i]), ratio, acc, vt);
             if (MODE == M_APEX) {   // vt[n_heavy + i]
                 unsigned long long d = acc.t - t0;
                 for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
@@ -599,13 +647,13 @@ __device__ uint32_t emit_sorted(const TrieView &tv, const uint32_t *A, uint32_t 
             bool hit = false;
             uint32_t a = 0;
             if (i < j) {
-                a = A[i];
+                a = ld_any(&A[i]);
                 if (probe) {
                     uint32_t x = a - base;
-                    hit = x < nbits && ((__ldg(&tv.words[dv.woff + (x >> 5)]) >> (x & 31)) & 1u);
+                    hit = x < nbits && ((ldg1(&tv.words[dv.woff + (x >> 5)]) >> (x & 31)) & 1u);
                 } else {
                     uint32_t pos = lower_bound(B, 0, dv.len, a);
-                    hit = pos < dv.len && __ldg(&B[pos]) == a;
+                    hit = pos < dv.len && ldg1(&B[pos]) == a;
                 }
             }
             uint32_t m = __ballot_sync(FULL, hit);
@@ -635,7 +683,7 @@ __device__ uint32_t emit_sorted(const TrieView &tv, const uint32_t *A, uint32_t 
             for (int k = 0; k < 4; ++k) {
                 if (w[k] == EH_PAD) continue;
                 uint32_t pos = lower_bound(A, lo, hi, w[k]);
-                if (pos < hi && A[pos] == w[k]) f |= 1u << k;
+                if (pos < hi && ld_any(&A[pos]) == w[k]) f |= 1u << k;
             }
         }
         uint32_t tot;
@@ -666,8 +714,8 @@ __device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t
     uint32_t s_lo = 0, s_nw = 0;
     bool bm = false;
     if (Sbm && ns >= 32) {
-        s_lo = (S[0] >> 7) << 2;
-        s_nw = (((S[ns - 1] >> 5) + 1 - s_lo) + 3) & ~3u;
+        s_lo = (ld_any(&S[0]) >> 7) << 2;
+        s_nw = (((ld_any(&S[ns - 1]) >> 5) + 1 - s_lo) + 3) & ~3u;
         bm = s_nw <= SB_CAP_WORDS && s_nw <= ns;
         if (bm && bm_lo != EH_PAD) {
             // level 1 left S's words [bm_lo, ...) in Sbm: S's own range starts inside it
@@ -676,7 +724,7 @@ __device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t
             for (uint32_t w = lane; w < s_nw; w += 32) Sbm[w] = 0u;
             __syncwarp();
             for (uint32_t k = lane; k < ns; k += 32) {
-                const uint32_t e = S[k];
+                const uint32_t e = ld_any(&S[k]);
                 atomicOr(&Sbm[(e >> 5) - s_lo], 1u << (e & 31));
             }
             __syncwarp();
@@ -684,7 +732,7 @@ __device__ __forceinline__ void clique_level2(const TrieView &tv, const uint32_t
     }
     for (uint32_t i0 = 1; i0 < ns; i0 += 32) {
         const uint32_t il = i0 + lane;
-        const SetDesc mine = il < ns ? tv.desc[S[il]] : empty_desc();
+        const SetDesc mine = il < ns ? ld_desc(&tv.desc[ld_any(&S[il])]) : empty_desc();
         const uint32_t cnt = min(32u, ns - i0);
         uint32_t coop = __ballot_sync(FULL, il < ns && mine.len > 0);
         if (bm) {
@@ -741,7 +789,7 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
                                          uint32_t *status, uint32_t *arena, uint64_t arena_per_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t gwarp = (uint64_t)blockIdx.x * WARPS + warp;
-    const SetDesc dx = tv.desc[x];
+    const SetDesc dx = ld_desc(&tv.desc[x]);
     if (threadIdx.x == 0) *s_next = 2;
     StagedA st;
     if (!stage_set<WARPS>(tv, dx, sA, mbar, phase, st, status)) return false;
@@ -750,7 +798,7 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
         if (j0 >= st.len) break;
         const uint32_t jl = j0 + lane;
         SetDesc mine = empty_desc();
-        if (lane < K4_PAIR_BATCH && jl < st.len) mine = tv.desc[st.amode == 0 ? __ldg(&st.Ag[jl]) : st.A[jl]];
+        if (lane < K4_PAIR_BATCH && jl < st.len) mine = ld_desc(&tv.desc[st.amode == 0 ? ldg1(&st.Ag[jl]) : ld_any(&st.A[jl])]);
         const uint32_t nbat = min(K4_PAIR_BATCH, st.len - j0);
         for (uint32_t i = 0; i < nbat; ++i) {
         const uint32_t j = j0 + i;
@@ -777,10 +825,10 @@ __device__ __forceinline__ bool k4_heavy(const TrieView &tv, uint32_t x, uint32_
 // light vertex x: A and S held one element per lane
 __device__ void k4_light(const TrieView &tv, uint32_t x, uint32_t ratio, Acc &acc) {
     const int lane = threadIdx.x & 31;
-    const SetDesc dx = tv.desc[x];
+    const SetDesc dx = ld_desc(&tv.desc[x]);
     const uint32_t k = dx.len;
-    const uint32_t a = lane < k ? __ldg(&tv.nbr[dx.off + lane]) : EH_PAD;
-    const SetDesc mine = lane < k ? tv.desc[a] : empty_desc();
+    const uint32_t a = lane < k ? ldg1(&tv.nbr[dx.off + lane]) : EH_PAD;
+    const SetDesc mine = lane < k ? ld_desc(&tv.desc[a]) : empty_desc();
     for (uint32_t j = 2; j < k; ++j) {
         const SetDesc dy = bcast_desc(mine, j);
         if (dy.len < 2) continue;
@@ -801,7 +849,7 @@ __device__ void k4_light(const TrieView &tv, uint32_t x, uint32_t ratio, Acc &ac
             const uint32_t e = __shfl_sync(FULL, sv, t2);
             const uint32_t x = e - zbase;
             if (lane_bits && t2 < (uint32_t)lane && x < znbits)
-                c += (__ldg(&tv.words[sd.woff + (x >> 5)]) >> (x & 31)) & 1u;
+                c += (ldg1(&tv.words[sd.woff + (x >> 5)]) >> (x & 31)) & 1u;
         }
         acc.t += c;
         uint32_t coop = __ballot_sync(FULL, (uint32_t)lane >= 1 && (uint32_t)lane < ns && sd.len > 0 && !sd.nwords);
@@ -829,14 +877,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
     const int tid = threadIdx.x, lane = tid & 31;
     Acc acc{0, 0};
     uint32_t phase = 0;
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        CHK_TRIE(tv, heavy, n_heavy, light, n_light, status);
+        CHK_ADD(arena, arena_per_warp * gridDim.x * WARPS * 4);
+    }
     __syncthreads();
     for (;;) {
         if (tid == 0) s_item = (uint32_t)min((unsigned long long)n_heavy, atomicAdd(&counters[0], 1ull));
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
-        if (!k4_heavy<WARPS>(tv, heavy[item], ratio, sA, sS, sB, &mbar, phase, &s_next, acc, status, arena,
+        if (!k4_heavy<WARPS>(tv, ldg1(&heavy[item]), ratio, sA, sS, sB, &mbar, phase, &s_next, acc, status, arena,
                              arena_per_warp))
             return;
     }
@@ -846,7 +898,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
         base = __shfl_sync(FULL, base, 0);
         if (base >= n_light) break;
         uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
-        for (uint32_t it = (uint32_t)base; it < end; ++it) k4_light(tv, __ldg(&light[it]), ratio, acc);
+        for (uint32_t it = (uint32_t)base; it < end; ++it) k4_light(tv, ldg1(&light[it]), ratio, acc);
     }
     unsigned long long t = acc.t;
     for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
@@ -864,12 +916,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
 
 __device__ __forceinline__ TrieView view_of(const BatchView &b, uint32_t q) {
     TrieView v;
-    const uint32_t base = b.qbase[q];
+    const uint32_t base = ldg1(&b.qbase[q]);
     v.desc = b.desc + base;
     v.nbr = b.nbr;
     v.words = b.words;
     v.deg = b.deg + base;
-    v.n = b.qbase[q + 1] - base;
+    v.n = ldg1(&b.qbase[q + 1]) - base;
     return v;
 }
 
@@ -888,18 +940,22 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch(BatchView bv, const uint32
     __shared__ unsigned long long red_t[WARPS], red_s[WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t phase = 0;
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        CHK_BATCH(bv, heavy, n_heavy, light, n_light, status);
+        CHK_ADD(arena, arena_per_warp * gridDim.x * WARPS * 4);
+    }
     __syncthreads();
     for (;;) {
         if (tid == 0) s_item = (uint32_t)min((unsigned long long)n_heavy, atomicAdd(&counters[0], 1ull));
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
-        const uint32_t sidx = heavy[item];
-        const uint32_t q = bv.sub_q[sidx];
+        const uint32_t sidx = ldg1(&heavy[item]);
+        const uint32_t q = ldg1(&bv.sub_q[sidx]);
         const TrieView tv = view_of(bv, q);
-        const uint32_t u = sidx - bv.qbase[q];
-        const uint32_t pat = bv.qpat[q];
+        const uint32_t u = sidx - ldg1(&bv.qbase[q]);
+        const uint32_t pat = ldg1(&bv.qpat[q]);
         Acc acc{0, 0};
         bool ok;
         if (pat == EH_CLIQUE4)
@@ -930,11 +986,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch(BatchView bv, const uint32
         if (base >= n_light) break;
         uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
         for (uint32_t it = (uint32_t)base; it < end; ++it) {
-            const uint32_t sidx = __ldg(&light[it]);
-            const uint32_t q = bv.sub_q[sidx];
+            const uint32_t sidx = ldg1(&light[it]);
+            const uint32_t q = ldg1(&bv.sub_q[sidx]);
             const TrieView tv = view_of(bv, q);
-            const uint32_t u = sidx - bv.qbase[q];
-            const uint32_t pat = bv.qpat[q];
+            const uint32_t u = sidx - ldg1(&bv.qbase[q]);
+            const uint32_t pat = ldg1(&bv.qpat[q]);
             Acc acc{0, 0};
             if (pat == EH_CLIQUE4) k4_light(tv, u, ratio, acc);
             else if (pat == EH_TRIANGLE) light_vertex<M_COUNT>(tv, u, ratio, acc, nullptr);

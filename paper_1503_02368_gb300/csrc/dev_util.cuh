@@ -15,7 +15,92 @@ constexpr uint32_t FULL = 0xffffffffu;
 constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;          // bounded wait for a bulk copy: iterations
 constexpr uint64_t MBAR_TIME_LIMIT_NS = 2000000000ull;  // ... and wall time (2 s)
 
-__device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+// ------------------------------------------------------------ load checks
+//
+// With EH_CHECK_LOADS defined (the checked build, libeh_check.so) every
+// global load of the count kernels goes through the functions below, which
+// verify that the bytes lie inside one of the arrays the kernel was given
+// (registered per CTA in shared memory by chk_register at kernel start).  A
+// load outside them is not made: it sets DEV_ST_BOUNDS in the kernel's status
+// word and yields a harmless value (EH_PAD elements, zero words, an empty
+// descriptor), so the run ends with an error status instead of a fault.
+// Without the flag they are plain read-only loads.
+#ifdef EH_CHECK_LOADS
+constexpr int CHK_MAX = 12;
+struct ChkTable {
+    uintptr_t lo[CHK_MAX], hi[CHK_MAX];   // byte ranges [lo, hi)
+    uint32_t *status;
+    int n;
+};
+static __shared__ ChkTable s_chk;
+
+// thread 0 of the CTA; the caller synchronises before the first checked load
+__device__ __forceinline__ void chk_reset(uint32_t *status) {
+    s_chk.n = 0;
+    s_chk.status = status;
+}
+__device__ __forceinline__ void chk_add(const void *p, uint64_t bytes) {
+    if (s_chk.n < CHK_MAX && p) {
+        s_chk.lo[s_chk.n] = (uintptr_t)p;
+        s_chk.hi[s_chk.n] = (uintptr_t)p + bytes;
+        ++s_chk.n;
+    }
+}
+__device__ __forceinline__ bool chk_ok(const void *p, uint32_t bytes) {
+    if (!__isGlobal(p)) return true;   // shared-memory operands are indexed by construction
+    const uintptr_t a = (uintptr_t)p;
+    for (int i = 0; i < s_chk.n; ++i)
+        if (a >= s_chk.lo[i] && a + bytes <= s_chk.hi[i]) return true;
+    if (s_chk.status) atomicOr(s_chk.status, DEV_ST_BOUNDS);
+    return false;
+}
+#endif
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
+#ifdef EH_CHECK_LOADS
+    if (!chk_ok(p, 16)) return make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+#endif
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// one 32-bit element or word (a miss in the checked build reads EH_PAD)
+__device__ __forceinline__ uint32_t ldg1(const uint32_t *p) {
+#ifdef EH_CHECK_LOADS
+    if (!chk_ok(p, 4)) return EH_PAD;
+#endif
+    return __ldg(p);
+}
+
+// a 32-bit element of a set that may be in shared or global memory
+__device__ __forceinline__ uint32_t ld_any(const uint32_t *p) {
+#ifdef EH_CHECK_LOADS
+    if (!chk_ok(p, 4)) return EH_PAD;
+#endif
+    return *p;
+}
+
+// a set descriptor (a miss in the checked build reads an empty one)
+__device__ __forceinline__ SetDesc ld_desc(const SetDesc *p) {
+#ifdef EH_CHECK_LOADS
+    if (!chk_ok(p, sizeof(SetDesc))) {
+        SetDesc d;
+        d.off = 0; d.len = 0; d.deg = 0; d.woff = 0; d.lo_word = 0; d.nwords = 0;
+        return d;
+    }
+#endif
+    return *p;
+}
+
+// the source of a bulk copy lies inside a registered array (always true
+// without the checked build)
+__device__ __forceinline__ bool bulk_src_ok(const void *p, uint32_t bytes) {
+#ifdef EH_CHECK_LOADS
+    return chk_ok(p, bytes);
+#else
+    (void)p; (void)bytes;
+    return true;
+#endif
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -64,11 +149,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity,
     return done != 0;
 }
 
-// smallest index i in [lo, hi) with A[i] >= key (A sorted), or hi
+// smallest index i in [lo, hi) with A[i] >= key (A sorted; shared or global), or hi
 __device__ __forceinline__ uint32_t lower_bound(const uint32_t *A, uint32_t lo, uint32_t hi, uint32_t key) {
     while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
-        if (A[mid] < key) lo = mid + 1; else hi = mid;
+#ifdef EH_CHECK_LOADS
+        const uint32_t am = chk_ok(&A[mid], 4) ? A[mid] : EH_PAD;
+#else
+        const uint32_t am = A[mid];
+#endif
+        if (am < key) lo = mid + 1; else hi = mid;
     }
     return lo;
 }

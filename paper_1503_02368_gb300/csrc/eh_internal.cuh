@@ -45,6 +45,7 @@ enum : uint32_t {
     DEV_ST_OVERFLOW = 2u,  // an accumulator passed 2^63
     DEV_ST_INVALID = 4u,   // an input id was out of range
     DEV_ST_RANGE = 8u,     // a listing row fell outside the range its count pass gave it (not written)
+    DEV_ST_BOUNDS = 16u,   // checked build (EH_CHECK_LOADS): a load outside its array (not made)
 };
 
 // Scratch layout of a whole-graph count (unsigned long long words of
@@ -86,6 +87,7 @@ struct TrieView {
     const uint32_t *words;  // bitset pool
     const uint32_t *deg;    // d(v), symmetric degree
     uint32_t n;
+    uint64_t n_nbr = 0, n_words = 0;   // array extents (the checked build's load checks)
 };
 
 // Concatenated induced sub-tries of a batch of queries (see count.cu).
@@ -97,6 +99,7 @@ struct BatchView {
     const uint32_t *sub_q;  // query of each sub-vertex
     const uint32_t *qbase;  // first sub-vertex of each query (n_queries + 1)
     const uint32_t *qpat;   // pattern of each query
+    uint64_t n_sub = 0, n_nbr = 0, n_words = 0, n_queries = 0;   // extents (checked build)
 };
 
 // per-pattern work lists (vertex ids, heaviest first)
@@ -161,6 +164,7 @@ struct eh_trie {
     TrieView view() const {
         TrieView v;
         v.desc = d_desc; v.nbr = d_onbr; v.words = d_words; v.deg = d_deg; v.n = n;
+        v.n_nbr = onbr_len; v.n_words = n_words;
         return v;
     }
 };

@@ -9,7 +9,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libeh.so")
+# EH_LIBRARY may name the checked build (libeh_check.so, the count kernels'
+# loads range-checked); it must exist like the default library
+_LIB_PATH = os.environ.get("EH_LIBRARY") or os.path.join(_HERE, "libeh.so")
 _lib = None
 
 PATTERNS = {"triangle": 0, "clique4": 1, "lollipop": 2, "lollipop_distinct": 3, "barbell": 4}
@@ -60,7 +62,8 @@ class Query(ctypes.Structure):
 class BatchProfile(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("sub_vertices", ctypes.c_uint64),
                 ("sub_set_elements", ctypes.c_uint64), ("heavy_items", ctypes.c_uint64),
-                ("light_items", ctypes.c_uint64), ("prepare_s", ctypes.c_double), ("count_s", ctypes.c_double)]
+                ("light_items", ctypes.c_uint64), ("prepare_s", ctypes.c_double), ("count_s", ctypes.c_double),
+                ("graph_reuses", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):

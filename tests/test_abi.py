@@ -86,6 +86,15 @@ def test_range_bounds_rejects_bad_parts_without_gpu():
         eh.range_bounds(np.ones(4, np.uint64), 0, 0)
 
 
+def test_checked_build_exports_the_same_symbols():
+    # libeh_check.so: the same library with the count kernels' loads range-checked
+    lib = os.path.join(ROOT, "paper_1503_02368_gb300", "libeh_check.so")
+    assert os.path.exists(lib)
+    L = ctypes.CDLL(lib)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
 def test_last_error_is_callable_without_gpu():
     L = eh.lib()
     assert isinstance(L.eh_last_error(), bytes)
@@ -104,16 +113,16 @@ def test_structs_match_header_sizes(tmp_path):
     # the sizes the C compiler gives the header's structs, against the binding's
     import subprocess
     src = tmp_path / "sizes.c"
-    src.write_text('#include <stdio.h>\n#include "eh.h"\nint main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", '
+    src.write_text('#include <stdio.h>\n#include "eh.h"\nint main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", '
                    'sizeof(eh_build_opts), sizeof(eh_exec_opts), sizeof(eh_query), sizeof(eh_trie_stats_t), '
-                   'sizeof(eh_count_info), sizeof(eh_server_stats)); return 0; }\n')
+                   'sizeof(eh_count_info), sizeof(eh_server_stats), sizeof(eh_batch_profile)); return 0; }\n')
     exe = tmp_path / "sizes"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert got == [ctypes.sizeof(ehmod.BuildOpts), ctypes.sizeof(ehmod.ExecOpts), ctypes.sizeof(ehmod.Query),
                    ctypes.sizeof(ehmod.TrieStats), ctypes.sizeof(ehmod.CountInfo),
-                   ctypes.sizeof(ehmod.ServerStats)]
+                   ctypes.sizeof(ehmod.ServerStats), ctypes.sizeof(ehmod.BatchProfile)]
 
 
 def test_missing_library_fails_loudly(monkeypatch):

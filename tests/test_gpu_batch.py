@@ -125,3 +125,20 @@ def test_rmat20_ego4096_workload(eh):
     for q, rec in gold["queries"].items():       # oracle counts of a sample, incl. the 4 largest
         assert pats[int(q)] == rec["pattern"]
         assert int(c0[int(q)]) == rec["count"], (q, rec)
+
+
+def test_batch_count_graph_is_reused_across_calls(eh, rmat12):
+    # each device batch's count phase is a CUDA graph; after the first, the
+    # calling thread's executable graph is updated in place and relaunched
+    g, o = rmat12
+    t = eh.Trie(g["src"], g["dst"], g["n"], tau=32)
+    off, pool = synth.ego_subsets(g["n"], g["src"], g["dst"], synth.key(3, 3), 8, 0, 16, 400)
+    pats = ["triangle", "clique4"] * 4
+    c0, s0 = t.count_batch(pats, off, pool)                   # instantiates (or reuses) the graph
+    c1, s1 = t.count_batch(pats, off, pool, mode=1)           # one device batch per query
+    prof = eh.batch_profile()
+    assert prof["batches"] == 8 and prof["graph_reuses"] >= 7
+    assert not s0.any() and not s1.any() and np.array_equal(c0, c1)
+    for q in range(8):
+        assert int(c1[q]) == o.induced(pool[off[q]:off[q + 1]]).count(pats[q])
+    t.close()

@@ -72,12 +72,64 @@ struct Acc {
 
 // --------------------------------------------------------------- matches
 
+// (per-vertex mode: cnt, when given, is the staged vertex's shared counter
+// array and r the position of w in its set; else w's global counter)
 template <int MODE>
 __device__ __forceinline__ void on_match(Acc &acc, uint32_t w, uint32_t duv, const TrieView &tv,
-                                         unsigned long long *vt) {
+                                         unsigned long long *vt, uint32_t *cnt = nullptr, uint32_t r = 0) {
     acc.t += 1;
     if (MODE == M_LOLLI) acc.s += duv + ldg1(&tv.deg[w]);
-    if (MODE == M_VERTEX) atomicAdd(&vt[w], 1ull);
+    if (MODE == M_VERTEX) {
+        if (cnt) atomicAdd(&cnt[r], 1u);
+        else atomicAdd(&vt[w], 1ull);
+    }
+}
+
+// Per-vertex triangle counts of a heavy vertex u (the barbell's and the
+// selection's triangle nodes, eh_vertex_triangles): the triangles of each
+// element of A = N+(u) are counted in shared memory, cnt[i] for A[i], and
+// added to the global counters once per element when u is done -- one
+// global atomic per (u, element) instead of one per triangle (hub vertices
+// sit in millions of triangles).  A match w in the on-chip bitmap is found at
+// position sP[g] + (bits before it in its 128-bit group g) of A.
+constexpr uint32_t VT_CAP = 2048;   // elements of A counted on chip
+struct RankStage {
+    uint32_t *cnt;       // nullptr: counts go straight to the global counters
+    const uint16_t *sP;  // set bits of the bitmap's groups [0, g)
+};
+// shared words of the staging: counters, group prefixes, one word per warp
+constexpr uint32_t VT_WORDS = VT_CAP + BM_CAP_WORDS / 8 + 32;
+
+__device__ __forceinline__ uint32_t popc4(const uint32_t *p) {
+    const uint4 g = *reinterpret_cast<const uint4 *>(p);
+    return __popc(g.x) + __popc(g.y) + __popc(g.z) + __popc(g.w);
+}
+
+// sP[g] = set bits of the 128-bit groups [0, g) of the bitmap sA (ng groups):
+// each warp scans its contiguous segment of groups in rounds of 32 after the
+// warps' totals are combined (contains a CTA barrier)
+template <int WARPS>
+__device__ __forceinline__ void bitmap_prefix(const uint32_t *sA, uint32_t ng, uint16_t *sP, uint32_t *s_tmp) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t seg = (ng + WARPS - 1) / WARPS, b = min(ng, warp * seg), e = min(ng, b + seg);
+    uint32_t c = 0;
+    for (uint32_t g = b + lane; g < e; g += 32) c += popc4(sA + 4 * g);
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if (lane == 0) s_tmp[warp] = c;
+    __syncthreads();
+    uint32_t run = 0;
+    for (uint32_t k = 0; k < warp; ++k) run += s_tmp[k];
+    for (uint32_t g0 = b; g0 < e; g0 += 32) {
+        const uint32_t g = g0 + lane;
+        const uint32_t x = g < e ? popc4(sA + 4 * g) : 0u;
+        uint32_t incl = x;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
+        }
+        if (g < e) sP[g] = (uint16_t)(run + incl - x);
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
 }
 
 // all set bits of x (value base + bit) are matches
@@ -135,16 +187,18 @@ __device__ __forceinline__ void pair_bitmap(const TrieView &tv, const uint32_t *
 }
 
 // A sorted array (shared or global), effective prefix A[0..j) ∩ B
+// (cnt: the per-vertex mode's shared counters of A, indexed like A, or nullptr)
 template <int MODE>
 __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *A, uint32_t j, const SetDesc &dv,
-                                            uint32_t duv, uint32_t ratio, Acc &acc, unsigned long long *vt) {
+                                            uint32_t duv, uint32_t ratio, Acc &acc, unsigned long long *vt,
+                                            uint32_t *cnt = nullptr) {
     const int lane = threadIdx.x & 31;
     if (dv.nwords && j <= dv.len) {   // uint ∩ bitset: probe A's elements
         const uint32_t *bw = tv.words + dv.woff;
         const uint32_t base = dv.lo_word * 32, nbits = dv.nwords * 32;
         for (uint32_t i = lane; i < j; i += 32) {
             uint32_t a = ld_any(&A[i]), x = a - base;
-            if (x < nbits && ((ldg1(&bw[x >> 5]) >> (x & 31)) & 1u)) on_match<MODE>(acc, a, duv, tv, vt);
+            if (x < nbits && ((ldg1(&bw[x >> 5]) >> (x & 31)) & 1u)) on_match<MODE>(acc, a, duv, tv, vt, cnt, i);
         }
         return;
     }
@@ -153,7 +207,7 @@ __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *
         for (uint32_t i = lane; i < j; i += 32) {
             uint32_t a = ld_any(&A[i]);
             uint32_t pos = lower_bound(B, 0, dv.len, a);
-            if (pos < dv.len && ldg1(&B[pos]) == a) on_match<MODE>(acc, a, duv, tv, vt);
+            if (pos < dv.len && ldg1(&B[pos]) == a) on_match<MODE>(acc, a, duv, tv, vt, cnt, i);
         }
         return;
     }
@@ -178,14 +232,14 @@ __device__ __forceinline__ void pair_sorted(const TrieView &tv, const uint32_t *
                 uint32_t a = ld_any(&A[i]);
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (w[k] == a) on_match<MODE>(acc, a, duv, tv, vt);
+                    if (w[k] == a) on_match<MODE>(acc, a, duv, tv, vt, cnt, i);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (w[k] == EH_PAD) continue;
                 uint32_t pos = lower_bound(A, lo, hi, w[k]);
-                if (pos < hi && ld_any(&A[pos]) == w[k]) on_match<MODE>(acc, w[k], duv, tv, vt);
+                if (pos < hi && ld_any(&A[pos]) == w[k]) on_match<MODE>(acc, w[k], duv, tv, vt, cnt, pos);
             }
         }
     }
@@ -303,8 +357,54 @@ __device__ __forceinline__ void bitmap_plan(const TrieView &tv, uint32_t a_lo, u
 template <int MODE, int PW = 1>
 __device__ __forceinline__ void run_plan(const TrieView &tv, const uint32_t *sA, uint32_t a_lo, uint32_t a_nw,
                                          uint32_t kind, int64_t base, uint32_t begin, uint32_t end, uint32_t duv,
-                                         Acc &acc, unsigned long long *vt, uint32_t part = 0) {
+                                         Acc &acc, unsigned long long *vt, uint32_t part = 0,
+                                         const RankStage *rs = nullptr) {
     const uint32_t lane4 = (threadIdx.x & 31) * 4;
+    if (MODE == M_VERTEX) {   // staged per-element counters (tri_heavy takes this path only with rs)
+        if (kind == 1) {
+            const uint32_t *bw = tv.words + base;
+            for (uint32_t i = begin + lane4; i < end; i += 128) {
+                const uint4 b = ldg4(bw + i);
+                const uint4 a = *reinterpret_cast<const uint4 *>(sA + (i - a_lo));
+                const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw4[4] = {b.x, b.y, b.z, b.w};
+                uint32_t p = rs->sP[(i - a_lo) >> 2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t x = aw[q] & bw4[q];
+                    acc.t += __popc(x);
+                    while (x) {
+                        const uint32_t bit = __ffs(x) - 1;
+                        x &= x - 1;
+                        atomicAdd(&rs->cnt[p + __popc(aw[q] & ((1u << bit) - 1u))], 1u);
+                    }
+                    p += __popc(aw[q]);
+                }
+            }
+        } else if (kind == 2) {
+            const uint32_t *bp = tv.nbr + base;
+            const uint32_t abase = a_lo * 32, nbits = a_nw * 32;
+            for (uint32_t p = lane4; p < end; p += 256) {
+                const uint4 e0 = ldg4(bp + p);
+                const uint4 e1 = p + 128 < end ? ldg4(bp + p + 128) : make_uint4(EH_PAD, EH_PAD, EH_PAD, EH_PAD);
+                const uint32_t w[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t x = w[c] - abase;
+                    if (x < nbits && ((sA[x >> 5] >> (x & 31)) & 1u)) {
+                        // the 128-bit group holding x: A's position of its first element, bits before x
+                        const uint4 g = *reinterpret_cast<const uint4 *>(sA + ((x >> 7) << 2));
+                        const uint32_t q = (x >> 5) & 3u;
+                        const uint32_t aw = q == 0 ? g.x : q == 1 ? g.y : q == 2 ? g.z : g.w;
+                        const uint32_t before = (q > 0 ? __popc(g.x) : 0u) + (q > 1 ? __popc(g.y) : 0u) +
+                                                (q > 2 ? __popc(g.z) : 0u);
+                        acc.t += 1;
+                        atomicAdd(&rs->cnt[rs->sP[x >> 7] + before + __popc(aw & ((1u << (x & 31)) - 1u))], 1u);
+                    }
+                }
+            }
+        }
+        return;
+    }
     if (kind == 1) {
         const uint32_t *bw = tv.words + base;
         for (uint32_t i = begin + part * 128 + lane4; i < end; i += 128 * PW) {
@@ -401,10 +501,12 @@ __device__ __forceinline__ uint32_t next_j(uint32_t *s_next, uint32_t batch = PA
 // (pair j, part p), p < PW, so that PW warps share each pair's B against the
 // on-chip bitmap (every PW-th step of its range each, run_plan); the other
 // dispatches run the whole pair in part 0.  PW = 1 is one pair per warp.
+// s_rank: VT_WORDS shared words for the per-vertex mode's staged counters, or
+// nullptr (then every match adds to its global counter)
 template <int MODE, int WARPS, int PW = 1>
 __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32_t ratio, uint32_t *sA,
                                           uint64_t *mbar, uint32_t &phase, uint32_t *s_next, Acc &acc,
-                                          uint32_t *status, unsigned long long *vt) {
+                                          uint32_t *status, unsigned long long *vt, uint32_t *s_rank = nullptr) {
     const int lane = threadIdx.x & 31;
     const SetDesc du = ld_desc(&tv.desc[u]);
     if (threadIdx.x == 0) *s_next = PW;   // the first unit of pair 1
@@ -412,6 +514,15 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
     if (!stage_set<WARPS>(tv, du, sA, mbar, phase, st, status)) return false;
     const uint32_t n_units = st.len * PW;
     const unsigned long long t_start = acc.t;   // u's triangles, added once per vertex (per-vertex mode)
+    RankStage rs{nullptr, nullptr};
+    if (MODE == M_VERTEX && s_rank && st.len <= VT_CAP) {
+        uint16_t *sP = reinterpret_cast<uint16_t *>(s_rank + VT_CAP);
+        for (uint32_t i = threadIdx.x; i < st.len; i += WARPS * 32) s_rank[i] = 0;
+        if (st.amode == 0) bitmap_prefix<WARPS>(sA, st.a_nw / 4, sP, s_rank + VT_CAP + BM_CAP_WORDS / 8);
+        __syncthreads();
+        rs.cnt = s_rank;
+        rs.sP = sP;
+    }
     for (;;) {
         const uint32_t j0 = next_j(s_next);   // first unit of this grab
         if (j0 >= n_units) break;
@@ -424,7 +535,7 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
             mine = ld_desc(&tv.desc[vl]);
         }
         const uint32_t nb = min(PAIR_BATCH, n_units - j0);
-        if (st.amode == 0 && MODE != M_VERTEX) {
+        if (st.amode == 0 && (MODE != M_VERTEX || rs.cnt)) {
             // each descriptor lane plans its unit's pair; the warp runs the plans in turn
             uint32_t pk, pb, pe;
             int64_t pbase;
@@ -433,9 +544,15 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
             for (uint32_t i = 0; i < nb; ++i) {
                 const uint32_t kind = __shfl_sync(FULL, pk, i);
                 if (kind == 0) continue;
+                const unsigned long long t0 = acc.t;
                 run_plan<MODE, PW>(tv, sA, st.a_lo, st.a_nw, kind, __shfl_sync(FULL, pbase, i),
                                    __shfl_sync(FULL, pb, i), __shfl_sync(FULL, pe, i),
-                                   MODE == M_LOLLI ? __shfl_sync(FULL, pduv, i) : 0u, acc, vt, (j0 + i) % PW);
+                                   MODE == M_LOLLI ? __shfl_sync(FULL, pduv, i) : 0u, acc, vt, (j0 + i) % PW, &rs);
+                if (MODE == M_VERTEX) {   // v = A[j] is at position j of A
+                    unsigned long long pc = acc.t - t0;
+                    for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
+                    if (lane == 0 && pc) atomicAdd(&rs.cnt[j0 + i], (uint32_t)pc);
+                }
             }
             continue;
         }
@@ -448,11 +565,14 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
             const uint32_t duv = du.deg + dv.deg;
             unsigned long long t0 = acc.t;
             if (st.amode == 0) pair_bitmap<MODE>(tv, sA, st.a_lo, st.a_nw, dv, duv, acc, vt);
-            else pair_sorted<MODE>(tv, st.A, j, dv, duv, ratio, acc, vt);
+            else pair_sorted<MODE>(tv, st.A, j, dv, duv, ratio, acc, vt, rs.cnt);
             if (MODE == M_VERTEX) {
                 unsigned long long pc = acc.t - t0;
                 for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(FULL, pc, d);
-                if (lane == 0 && pc) atomicAdd(&vt[v], pc);
+                if (lane == 0 && pc) {
+                    if (rs.cnt) atomicAdd(&rs.cnt[j], (uint32_t)pc);
+                    else atomicAdd(&vt[v], pc);
+                }
             }
         }
     }
@@ -460,10 +580,21 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
         unsigned long long tu = acc.t - t_start;
         for (int d = 16; d > 0; d >>= 1) tu += __shfl_xor_sync(FULL, tu, d);
         if (lane == 0 && tu) atomicAdd(&vt[u], tu);
+        if (rs.cnt) {   // the elements' counts, once each
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < st.len; i += WARPS * 32) {
+                const uint32_t c = rs.cnt[i];
+                if (c) atomicAdd(&vt[ldg1(&st.Ag[i])], (unsigned long long)c);
+            }
+        }
     }
     __syncthreads();
     return true;
 }
+
+// dynamic shared memory of k_triangle: the staged A, and for the per-vertex
+// mode its elements' counters and group prefixes
+constexpr int tri_smem_bytes(int mode) { return (int)(BM_CAP_WORDS + (mode == M_VERTEX ? VT_WORDS : 0)) * 4; }
 
 // counters[0]: next heavy item, counters[1]: next light chunk
 template <int MODE, int WARPS, int PW = 1>
@@ -492,7 +623,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         const uint32_t item = s_item;
         if (item >= n_heavy) break;
         const unsigned long long t0 = acc.t;
-        if (!tri_heavy<MODE, WARPS, PW>(tv, ldg1(&heavy[item]), ratio, sA, &mbar, phase, &s_next, acc, status, vt)) return;
+        if (!tri_heavy<MODE, WARPS, PW>(tv, ldg1(&heavy[item]), ratio, sA, &mbar, phase, &s_next, acc, status, vt,
+                                        MODE == M_VERTEX ? sA + BM_CAP_WORDS : nullptr))
+            return;
         if (MODE == M_APEX) {   // this vertex's triangles (as the largest id) to vt[item]
             unsigned long long d = acc.t - t0;
             for (int k = 16; k > 0; k >>= 1) d += __shfl_xor_sync(FULL, d, k);
@@ -1065,7 +1198,7 @@ eh_status launch_tri(const WorkPlan &plan, TrieView tv, const eh_exec_opts &xo, 
                      unsigned long long *d_acc, unsigned long long *d_counters, uint32_t *d_status,
                      unsigned long long *d_vt) {
     auto kern = k_triangle<MODE, WARPS, PW>;
-    const int smem = BM_CAP_WORDS * 4;
+    const int smem = tri_smem_bytes(MODE);
     static bool attr_set = false;
     if (!attr_set) {
         EH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

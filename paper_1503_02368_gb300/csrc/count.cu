@@ -491,6 +491,15 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
 
 constexpr uint32_t PAIR_BATCH = 4;   // pairs a warp takes at a time from its CTA's vertex
 
+// light items a warp takes per grab: 32 when the list gives every resident
+// warp at least 4 such grabs (the atomic amortised), fewer on short lists so
+// that the items spread over more warps (small graphs, small batches)
+__device__ __forceinline__ uint32_t light_chunk(uint32_t n_light, uint32_t warps_per_cta) {
+    const uint64_t warps = (uint64_t)gridDim.x * warps_per_cta;
+    const uint64_t c = n_light / (4 * warps);
+    return c >= 32 ? 32u : c < 1 ? 1u : (uint32_t)c;
+}
+
 __device__ __forceinline__ uint32_t next_j(uint32_t *s_next, uint32_t batch = PAIR_BATCH) {
     uint32_t j = 0;
     if ((threadIdx.x & 31) == 0) j = atomicAdd(s_next, batch);
@@ -639,13 +648,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_triangle(TrieView tv, const uint
         }
     }
 
-    // light vertices: one warp each, taken 32 at a time
+    // light vertices: one warp each
+    const uint32_t chunk = light_chunk(n_light, WARPS);
     for (;;) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&counters[1], 32ull);
+        if (lane == 0) base = atomicAdd(&counters[1], (unsigned long long)chunk);
         base = __shfl_sync(FULL, base, 0);
         if (base >= n_light) break;
-        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
+        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + chunk);
         for (uint32_t i = (uint32_t)base; i < end; ++i) {
             const unsigned long long t0 = acc.t;
             light_vertex<MODE>(tv, ldg1(&light[i]), ratio, acc, vt);
@@ -1025,12 +1035,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique4(TrieView tv, const uint3
                              arena_per_warp))
             return;
     }
+    const uint32_t chunk = light_chunk(n_light, WARPS);
     for (;;) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&counters[1], 32ull);
+        if (lane == 0) base = atomicAdd(&counters[1], (unsigned long long)chunk);
         base = __shfl_sync(FULL, base, 0);
         if (base >= n_light) break;
-        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
+        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + chunk);
         for (uint32_t it = (uint32_t)base; it < end; ++it) k4_light(tv, ldg1(&light[it]), ratio, acc);
     }
     unsigned long long t = acc.t;
@@ -1112,12 +1123,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch(BatchView bv, const uint32
             if (S) atomicAdd(&out[2 * q + 1], S);
         }
     }
+    const uint32_t chunk = light_chunk(n_light, WARPS);
     for (;;) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&counters[1], 32ull);
+        if (lane == 0) base = atomicAdd(&counters[1], (unsigned long long)chunk);
         base = __shfl_sync(FULL, base, 0);
         if (base >= n_light) break;
-        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + 32);
+        uint32_t end = (uint32_t)min((unsigned long long)n_light, base + chunk);
         for (uint32_t it = (uint32_t)base; it < end; ++it) {
             const uint32_t sidx = ldg1(&light[it]);
             const uint32_t q = ldg1(&bv.sub_q[sidx]);

@@ -60,6 +60,9 @@ def parse():
                          "4-clique, query batch, serving) as extra keys; triangle: the headline only; all: default "
                          "plus the listing and the ordering study; any other name: the headline plus that leg")
     ap.add_argument("--serve-queries", type=int, default=1500)
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="process group of the N > 1 path (nccl: the 8-byte sum on the device; gloo: through the "
+                         "host, which also lets several ranks share one GPU)")
     return ap.parse_args()
 
 
@@ -742,12 +745,16 @@ def run_eh(args):
     import torch
 
     world, rank, local = dist_env()
+    local = local % max(1, torch.cuda.device_count())   # ranks beyond the GPU count share GPUs (gloo only)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group("gloo")
     import paper_1503_02368_gb300 as eh
     from synth import workloads as W
 

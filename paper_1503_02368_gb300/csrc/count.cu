@@ -315,9 +315,10 @@ __device__ void light_vertex(const TrieView &tv, uint32_t u, uint32_t ratio, Acc
 // ------------------------------------------------------------ heavy items
 //
 // A heavy vertex gets the whole CTA: A = N+(u) is staged once (bitset words
-// copied by cp.async.bulk, or a bitmap built from the uint array when its
-// range fits, or the sorted array copied by cp.async.bulk), then the warps
-// take the v = A[j] dynamically through a shared counter.
+// copied by cp.async.bulk when A is stored as a bitset of at most 4 words per
+// element, or a bitmap built from the uint array when its range fits, or the
+// sorted array copied by cp.async.bulk), then the warps take the v = A[j]
+// dynamically through a shared counter.
 
 struct StagedA {
     const uint32_t *Ag;   // A in global memory
@@ -443,7 +444,11 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
     st.a_lo = (first >> 7) << 2;
     st.a_nw = (((last >> 5) + 1 - st.a_lo) + 3) & ~3u;
     bool copy = false;
-    if (du.nwords && du.nwords <= BM_CAP_WORDS && bulk_src_ok(tv.words + du.woff, du.nwords * 4)) {
+    // a stored bitset is copied whole when it is not much larger than the uint
+    // array (at most 4 words per element); a sparser one is rebuilt on chip from
+    // the elements below, which reads 4|A| bytes instead of 4 x its words
+    if (du.nwords && du.nwords <= BM_CAP_WORDS && du.nwords <= 4ull * du.len &&
+        bulk_src_ok(tv.words + du.woff, du.nwords * 4)) {
         st.amode = 0;
         st.a_lo = du.lo_word;
         st.a_nw = du.nwords;

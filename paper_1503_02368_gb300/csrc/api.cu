@@ -1,4 +1,5 @@
-// api.cu -- the whole-graph entry points of eh.h and shared runtime helpers.
+// api.cu -- the whole-graph entry points of eh.h (counts, range counts, work-plan
+// facts, per-vertex counts, selections) and shared runtime helpers.
 #include "eh_internal.cuh"
 
 #include <algorithm>

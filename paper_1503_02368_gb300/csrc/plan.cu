@@ -1,6 +1,8 @@
 // plan.cu -- the per-vertex work list of the pruned trie (cost estimate,
-// light/heavy split by |N+(u)|, heaviest first) and, on request, the
-// algorithmic byte count of one triangle pass.
+// light/heavy split by |N+(u)|, heaviest first), the split of its lists into
+// cost-balanced ranges for counts divided among workers, and, on request,
+// the algorithmic byte counts of one pass (triangle lower bound, triangle at
+// the stored layouts' sizes, 4-clique lower bound).
 #include "eh_internal.cuh"
 
 namespace {

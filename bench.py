@@ -651,9 +651,21 @@ def bench_serve(eh, local, n_queries=1500, tau=32):
     ok_status = all(s_ == 0 for _, s_ in out)
     # each result equals the query alone, and the oracle's sampled queries
     rng = np.random.default_rng(0)
-    sample = rng.choice(n_queries, size=min(64, n_queries), replace=False)
-    alone_ok = all(trie.count(pats[q], subset=subsets[q]) == counts[q] for q in sample)
+    sample = rng.choice(n_queries, size=min(256, n_queries), replace=False)
+    # the same queries one at a time (eh_count over the subset: one device batch,
+    # one count launch per query): equal results, and the plain baseline's rate
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    alone = [trie.count(pats[q], subset=subsets[q]) for q in sample]
+    torch.cuda.synchronize()
+    t_alone = time.perf_counter() - t0
+    alone_ok = all(alone[i] == counts[q] for i, q in enumerate(sample))
     res["same_alone_and_in_mix"] = bool(alone_ok and ok_status)
+    res["one_query_at_a_time_qps"] = len(sample) / t_alone
+    res["one_query_at_a_time_sample"] = "%d queries drawn uniformly from the %d, run one after another" % (
+        len(sample), n_queries)
+    res["speedup_vs_one_at_a_time"] = sat / res["one_query_at_a_time_qps"]
     gold = golden("rmat_s24_serve")
     gq = {int(q): v for q, v in gold["queries"].items() if int(q) < n_queries}
     res["exact_vs_oracle_sample"] = all(counts[q] == v["count"] and pats[q] == v["pattern"] for q, v in gq.items())

@@ -212,14 +212,44 @@ __global__ void k_bclass(const SetDesc *__restrict__ desc, uint32_t V, uint32_t 
     flags[s] = (cls == 0 ? len > light_max : (len >= 2 && len <= light_max)) ? 1u : 0u;
 }
 
+// a query's total cost (warps aggregate their sub-vertices of one query:
+// a query's sub-vertices are contiguous)
+__global__ void k_bqcost(const uint64_t *__restrict__ cost, const uint32_t *__restrict__ sub_q, uint32_t V,
+                         unsigned long long *qcost) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < V;
+    const uint32_t q = valid ? sub_q[s] : 0xFFFFFFFFu;
+    unsigned long long c = valid ? cost[s] : 0ull;
+    const uint32_t peers = __match_any_sync(FULLM, q);
+    const uint32_t lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long y = __shfl_down_sync(FULLM, c, d);
+        const uint32_t src = lane + d;
+        if (src < 32 && ((peers >> src) & 1u)) c += y;   // peers are a contiguous run of lanes
+    }
+    if (valid && lane == leader && c) atomicAdd(&qcost[q], c);
+}
+
+// cost on a 14-bit logarithmic scale (exponent and the next 8 bits)
+constexpr int BCOST_BITS = 14;
+__device__ __forceinline__ uint32_t log_cost(uint64_t c) {
+    if (!c) return 0;
+    const int msb = 63 - __clzll((long long)c);
+    return (uint32_t)msb * 256u + (uint32_t)(((c << (63 - msb)) >> 55) & 255u);
+}
+
+// Work-list order: query by query (qrank: the queries by total cost, heaviest
+// first), and within a query its sub-vertices by cost, heaviest first.  The
+// CTAs then work on one query's sub-trie at a time, which stays in L2, while
+// the heaviest items still come first.
 __global__ void k_bkeys(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos,
-                        const uint64_t *__restrict__ cost, uint32_t V, int vb, uint64_t *keys) {
+                        const uint64_t *__restrict__ cost, const uint32_t *__restrict__ sub_q,
+                        const uint32_t *__restrict__ qrank, uint32_t V, int vb, uint64_t *keys) {
     uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V || !flags[s]) return;
-    const int cbits = 63 - vb < 40 ? 63 - vb : 40;
-    uint64_t cmax = (1ull << cbits) - 1;
-    uint64_t c = cost[s] < cmax ? cost[s] : cmax;
-    keys[pos[s]] = ((cmax - c) << vb) | s;
+    const uint64_t cmax = (1ull << BCOST_BITS) - 1;
+    const uint64_t c = cmax - log_cost(cost[s]);
+    keys[pos[s]] = (((uint64_t)qrank[sub_q[s]] << BCOST_BITS | c) << vb) | s;
 }
 
 __global__ void k_bids(const uint64_t *__restrict__ keys, uint32_t cnt, int vb, uint32_t *ids) {
@@ -251,8 +281,9 @@ struct Scratch {
     }
 };
 
-eh_status sorted_list(const SetDesc *desc, const uint64_t *cost, uint32_t V, uint32_t light_max, int cls,
-                      cudaStream_t s, Scratch &sc, uint32_t **out, uint32_t *count) {
+eh_status sorted_list(const SetDesc *desc, const uint64_t *cost, const uint32_t *sub_q, const uint32_t *qrank,
+                      uint32_t nq, uint32_t V, uint32_t light_max, int cls, cudaStream_t s, Scratch &sc,
+                      uint32_t **out, uint32_t *count) {
     uint32_t *flags = nullptr, *pos = nullptr;
     EH_TRY(sc.alloc(&flags, V));
     EH_TRY(sc.alloc(&pos, V));
@@ -264,10 +295,11 @@ eh_status sorted_list(const SetDesc *desc, const uint64_t *cost, uint32_t V, uin
     EH_TRY(sc.alloc(&k1, cnt));
     EH_TRY(sc.alloc(&k2, cnt));
     EH_TRY(sc.alloc(&ids, cnt));
-    const int vb = bits_of((uint64_t)V + 1);
+    const int vb = bits_of((uint64_t)V + 1), qb = bits_of((uint64_t)nq + 1);
+    if (vb + qb + BCOST_BITS > 64) { eh_set_error("batch: too many sub-vertices for the work-list key"); return EH_EINVAL; }
     if (cnt) {
-        k_bkeys<<<nblk(V), 256, 0, s>>>(flags, pos, cost, V, vb, k1);
-        EH_TRY(dev_radix_sort_u64(&k1, &k2, cnt, vb + (63 - vb < 40 ? 63 - vb : 40), s));
+        k_bkeys<<<nblk(V), 256, 0, s>>>(flags, pos, cost, sub_q, qrank, V, vb, k1);
+        EH_TRY(dev_radix_sort_u64(&k1, &k2, cnt, vb + qb + BCOST_BITS, s));
         k_bids<<<nblk(cnt), 256, 0, s>>>(k1, (uint32_t)cnt, vb, ids);
     }
     *out = ids;
@@ -397,9 +429,24 @@ eh_status run_batch(eh_trie *t, const eh_query *queries, const std::vector<uint3
     uint64_t *cost = nullptr;
     EH_TRY(sc.alloc(&cost, V));
     if (V) k_bcost<<<nblk(V, 8), 256, 0, s>>>(bv, V, cost);
+    // the queries ranked by total cost, heaviest first (the lists' outer order)
+    unsigned long long *d_qc = nullptr;
+    uint32_t *d_qrank = nullptr;
+    EH_TRY(sc.alloc(&d_qc, nq));
+    EH_TRY(sc.alloc(&d_qrank, nq));
+    EH_CUDA_TRY(cudaMemsetAsync(d_qc, 0, (uint64_t)nq * 8, s));
+    if (V) k_bqcost<<<nblk(V), 256, 0, s>>>(cost, sub_q, V, d_qc);
+    std::vector<unsigned long long> h_qc(nq);
+    std::vector<uint32_t> order(nq), h_qrank(nq);
+    EH_CUDA_TRY(cudaMemcpyAsync(h_qc.data(), d_qc, (uint64_t)nq * 8, cudaMemcpyDeviceToHost, s));
+    EH_CUDA_TRY(cudaStreamSynchronize(s));
+    for (uint32_t i = 0; i < nq; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return h_qc[a] > h_qc[b]; });
+    for (uint32_t r = 0; r < nq; ++r) h_qrank[order[r]] = r;
+    EH_CUDA_TRY(cudaMemcpyAsync(d_qrank, h_qrank.data(), (uint64_t)nq * 4, cudaMemcpyHostToDevice, s));
     uint32_t *heavy = nullptr, *light = nullptr, n_heavy = 0, n_light = 0;
-    EH_TRY(sorted_list(desc, cost, V, xo.light_max, 0, s, sc, &heavy, &n_heavy));
-    EH_TRY(sorted_list(desc, cost, V, xo.light_max, 1, s, sc, &light, &n_light));
+    EH_TRY(sorted_list(desc, cost, sub_q, d_qrank, nq, V, xo.light_max, 0, s, sc, &heavy, &n_heavy));
+    EH_TRY(sorted_list(desc, cost, sub_q, d_qrank, nq, V, xo.light_max, 1, s, sc, &light, &n_light));
 
     // 4-clique arena when a materialised S may exceed the shared buffer
     uint32_t *dmax = nullptr;

@@ -496,6 +496,39 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
 
 constexpr uint32_t PAIR_BATCH = 4;   // pairs a warp takes at a time from its CTA's vertex
 
+// One grab of the count modes against the on-chip bitmap: a quarter warp per
+// pair.  The quarter's 8 lanes load its pair's descriptor (one address a
+// quarter) and plan it; the AND pairs then run side by side, 8 lanes x 4
+// words a step with the four pairs' loads in flight together, and the probe
+// pairs one after another on the whole warp.  Against one pair per warp in
+// turn this drops the per-pair broadcasts and most steps of short AND pairs
+// (half of them are 80 words or fewer on R-MAT).
+static_assert(PAIR_BATCH == 4, "one quarter warp per pair of a grab");
+template <int MODE>
+__device__ __forceinline__ void quarter_grab(const TrieView &tv, const uint32_t *sA, const StagedA &st, uint32_t j0,
+                                             Acc &acc, unsigned long long *vt) {
+    const uint32_t lane = threadIdx.x & 31, jq = j0 + (lane >> 3);
+    uint32_t kind = 0, b = 0, e = 0;
+    int64_t base = 0;
+    if (jq < st.len) bitmap_plan(tv, st.a_lo, st.a_nw, ld_desc(&tv.desc[ldg1(&st.Ag[jq])]), kind, base, b, e);
+    if (kind == 1) {
+        const uint32_t *bw = tv.words + base;
+        uint32_t c = 0;
+        for (uint32_t i = b + (lane & 7) * 4; i < e; i += 32) {
+            const uint4 bv = ldg4(bw + i);
+            const uint4 av = *reinterpret_cast<const uint4 *>(sA + (i - st.a_lo));
+            c += __popc(av.x & bv.x) + __popc(av.y & bv.y) + __popc(av.z & bv.z) + __popc(av.w & bv.w);
+        }
+        acc.t += c;
+    }
+    __syncwarp();
+    for (uint32_t q = 0; q < 4; ++q) {
+        if (__shfl_sync(FULL, kind, 8 * q) != 2) continue;
+        run_plan<MODE, 1>(tv, sA, st.a_lo, st.a_nw, 2u, __shfl_sync(FULL, base, 8 * q), 0u,
+                          __shfl_sync(FULL, e, 8 * q), 0u, acc, vt);
+    }
+}
+
 // light items a warp takes per grab: 32 when the list gives every resident
 // warp at least 4 such grabs (the atomic amortised), fewer on short lists so
 // that the items spread over more warps (small graphs, small batches)
@@ -540,6 +573,12 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
     for (;;) {
         const uint32_t j0 = next_j(s_next);   // first unit of this grab
         if (j0 >= n_units) break;
+        if constexpr ((MODE == M_COUNT || MODE == M_APEX) && PW == 1) {
+            if (st.amode == 0) {
+                quarter_grab<MODE>(tv, sA, st, j0, acc, vt);
+                continue;
+            }
+        }
         // the next PAIR_BATCH units: their pair's v and descriptor loaded one per lane
         const uint32_t jl = (j0 + lane) / PW;
         uint32_t vl = 0;

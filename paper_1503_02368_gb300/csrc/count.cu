@@ -496,28 +496,40 @@ __device__ __forceinline__ bool stage_set(const TrieView &tv, const SetDesc &du,
 
 constexpr uint32_t PAIR_BATCH = 4;   // pairs a warp takes at a time from its CTA's vertex
 
-// One grab of the count modes against the on-chip bitmap: a quarter warp per
-// pair.  The quarter's 8 lanes load its pair's descriptor (one address a
-// quarter) and plan it; the AND pairs then run side by side, 8 lanes x 4
-// words a step with the four pairs' loads in flight together, and the probe
-// pairs one after another on the whole warp.  Against one pair per warp in
-// turn this drops the per-pair broadcasts and most steps of short AND pairs
-// (half of them are 80 words or fewer on R-MAT).
+// One grab of the count and lollipop modes against the on-chip bitmap: a
+// quarter warp per pair.  The quarter's 8 lanes load its pair's descriptor
+// (one address a quarter) and plan it; the AND pairs then run side by side,
+// 8 lanes x 4 words a step with the four pairs' loads in flight together, and
+// the probe pairs one after another on the whole warp.  Against one pair per
+// warp in turn this drops the per-pair broadcasts and most steps of short AND
+// pairs (half of them are 80 words or fewer on R-MAT).  The lollipop walks
+// the set bits of its AND words, each match adding d(u) + d(v) + d(w).
 static_assert(PAIR_BATCH == 4, "one quarter warp per pair of a grab");
 template <int MODE>
 __device__ __forceinline__ void quarter_grab(const TrieView &tv, const uint32_t *sA, const StagedA &st, uint32_t j0,
-                                             Acc &acc, unsigned long long *vt) {
+                                             uint32_t du_deg, Acc &acc, unsigned long long *vt) {
     const uint32_t lane = threadIdx.x & 31, jq = j0 + (lane >> 3);
-    uint32_t kind = 0, b = 0, e = 0;
+    uint32_t kind = 0, b = 0, e = 0, duv = 0;
     int64_t base = 0;
-    if (jq < st.len) bitmap_plan(tv, st.a_lo, st.a_nw, ld_desc(&tv.desc[ldg1(&st.Ag[jq])]), kind, base, b, e);
+    if (jq < st.len) {
+        const SetDesc dq = ld_desc(&tv.desc[ldg1(&st.Ag[jq])]);
+        bitmap_plan(tv, st.a_lo, st.a_nw, dq, kind, base, b, e);
+        if constexpr (MODE == M_LOLLI) duv = du_deg + dq.deg;
+    }
     if (kind == 1) {
         const uint32_t *bw = tv.words + base;
         uint32_t c = 0;
         for (uint32_t i = b + (lane & 7) * 4; i < e; i += 32) {
             const uint4 bv = ldg4(bw + i);
             const uint4 av = *reinterpret_cast<const uint4 *>(sA + (i - st.a_lo));
-            c += __popc(av.x & bv.x) + __popc(av.y & bv.y) + __popc(av.z & bv.z) + __popc(av.w & bv.w);
+            if constexpr (MODE == M_LOLLI) {
+                on_word<MODE>(acc, av.x & bv.x, i * 32, duv, tv, vt);
+                on_word<MODE>(acc, av.y & bv.y, i * 32 + 32, duv, tv, vt);
+                on_word<MODE>(acc, av.z & bv.z, i * 32 + 64, duv, tv, vt);
+                on_word<MODE>(acc, av.w & bv.w, i * 32 + 96, duv, tv, vt);
+            } else {
+                c += __popc(av.x & bv.x) + __popc(av.y & bv.y) + __popc(av.z & bv.z) + __popc(av.w & bv.w);
+            }
         }
         acc.t += c;
     }
@@ -525,7 +537,7 @@ __device__ __forceinline__ void quarter_grab(const TrieView &tv, const uint32_t 
     for (uint32_t q = 0; q < 4; ++q) {
         if (__shfl_sync(FULL, kind, 8 * q) != 2) continue;
         run_plan<MODE, 1>(tv, sA, st.a_lo, st.a_nw, 2u, __shfl_sync(FULL, base, 8 * q), 0u,
-                          __shfl_sync(FULL, e, 8 * q), 0u, acc, vt);
+                          __shfl_sync(FULL, e, 8 * q), MODE == M_LOLLI ? __shfl_sync(FULL, duv, 8 * q) : 0u, acc, vt);
     }
 }
 
@@ -573,9 +585,9 @@ __device__ __forceinline__ bool tri_heavy(const TrieView &tv, uint32_t u, uint32
     for (;;) {
         const uint32_t j0 = next_j(s_next);   // first unit of this grab
         if (j0 >= n_units) break;
-        if constexpr ((MODE == M_COUNT || MODE == M_APEX) && PW == 1) {
+        if constexpr ((MODE == M_COUNT || MODE == M_APEX || MODE == M_LOLLI) && PW == 1) {
             if (st.amode == 0) {
-                quarter_grab<MODE>(tv, sA, st, j0, acc, vt);
+                quarter_grab<MODE>(tv, sA, st, j0, du.deg, acc, vt);
                 continue;
             }
         }

@@ -230,7 +230,7 @@ eh_status eh_count_status(const eh_trie *trie, void *stream);
  *               (each a sum over the outer vertices); EH_BARBELL is EH_EINVAL
  *   part        0 .. nparts-1; nparts >= 1 (else EH_EINVAL)
  *   out_count   host uint64: this part's share.  The call synchronises `stream`.
- * The work plan's heavy and light lists (heaviest first) are each cut into
+ * The work plan's heavy and light lists (in their locality order) are each cut into
  * nparts contiguous ranges of about equal estimated cost (per vertex u,
  * sum over v in N+(u) of |N+(v)|; as eh_range_bounds); the first call on a
  * plan copies the lists' cost prefix sums to the host (8 bytes per listed

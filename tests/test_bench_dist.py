@@ -48,7 +48,7 @@ def _part_worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     rng = np.random.default_rng(5)
-    cost = np.sort(rng.integers(0, 5000, size=3000))[::-1].astype(np.uint64)   # heaviest first, as the plan
+    cost = np.sort(rng.integers(0, 5000, size=3000))[::-1].astype(np.uint64)   # per-item cost estimates
     per_item = rng.integers(0, 100, size=3000).astype(np.int64)                 # each item's partial count
     mine = bench.part_count_host(cost, per_item, rank, world)
     t = bench.sum_over_ranks_(torch.tensor([mine], dtype=torch.int64), world)

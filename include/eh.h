@@ -142,7 +142,10 @@ typedef struct {
     /* warps per intersection: how many warps of a heavy vertex's CTA share one
      * pair (u, v), each taking every pair_warps-th step of N+(v) against the
      * staged N+(u) (1, 2 or 4; default 1).  Whole-graph triangle and lollipop
-     * counts; the other patterns take one warp per pair. */
+     * counts; the other patterns take one warp per pair.  At 1, when N+(u) is
+     * staged as a bitmap, the triangle and lollipop counts give each of the
+     * four pairs a warp takes at a time a quarter warp (8 lanes) for the word
+     * AND pairs, and the whole warp for the others. */
     uint32_t pair_warps;
 } eh_exec_opts;
 
